@@ -1,0 +1,290 @@
+"""Benchmark: uint32 keys sorted per second at n = 2^28 on GB300.
+
+One step = one full bitonic sort (every launch of the plan) of one array of
+uniform random uint32 keys already resident in HBM.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (launched by torch.distributed.run): every rank sorts its own array
+(replicas, weak scaling; the sort has no cross-GPU exchange step).
+
+--impl reference times the CPU oracle (the paper's network, plain C, one
+core) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "uint32 Gkeys/s at n=2^28 (% HBM roofline); batched vs per-array speedup; p99"
+UNIT = "Gkeys/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-log2", type=int, default=28, help="keys per array = 2^n_log2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the e2e / per-kernel legs")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """The CPU oracle (Section 3.1 network, plain C, one core) on a bounded
+    sample of the workload: each step sorts 2^20 uniform keys."""
+    if rank != 0:
+        return
+    import oracle
+
+    n_sample = 1 << 20
+    keys = workloads.uniform_u32(n_sample, seed=workloads.SEEDS["n28_uniform"])
+    for _ in range(args.warmup):
+        oracle.bitonic_sort(keys)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.bitonic_sort(keys)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n_sample * args.steps / total / 1e9
+    sample = f"{args.steps} x 2^20 uniform uint32 keys (bounded sample of the 2^28 workload)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (splitmix64 uniform uint32)",
+        "config": {"workload": "uniform uint32 sort, CPU oracle sample", "n": n_sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline():
+    """Oracle network on one host core, ~10-20 s of work: 2^22 keys, repeated."""
+    import oracle
+
+    n = 1 << 22
+    keys = workloads.uniform_u32(n, seed=workloads.SEEDS["n28_uniform"])
+    reps, total = 0, 0.0
+    while total < 10.0 and reps < 8:
+        t0 = time.perf_counter()
+        oracle.bitonic_sort(keys)
+        total += time.perf_counter() - t0
+        reps += 1
+    return {"value": n * reps / total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x 2^22 uniform uint32 keys, Section 3.1 network in plain C"}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import paper_1506_01446_gb300 as bt
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = 1 << args.n_log2
+    hbm_gbs, peak_src = load_peaks()
+    keys_np = workloads.uniform_u32(n, seed=workloads.SEEDS["n28_uniform"] + rank)
+    pristine = torch.from_numpy(keys_np.view(np.int32)).cuda()
+    buf = pristine.clone()
+    stream = torch.cuda.current_stream()
+    info = bt.plan_info(n)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also builds and caches the CUDA graph)
+    for _ in range(args.warmup):
+        buf.copy_(pristine)
+        bt.sort_(buf)
+    barrier()
+    check = buf[:: max(1, n // 4096)].cpu().numpy().view(np.uint32)
+    assert np.all(check[1:] >= check[:-1]), "output not sorted"
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        for i in range(args.steps):
+            buf.copy_(pristine)  # restore the unsorted input (not timed)
+            starts[i].record(stream)
+            bt.sort_(buf)
+            ends[i].record(stream)
+        barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = n * world * args.steps / (total_ms / 1e3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (splitmix64 uniform uint32, input restored before every step, untimed)",
+        "config": {"workload": f"single uint32 array, n=2^{args.n_log2}, uniform random, ascending",
+                   "n": n, "l2": "inputs larger than L2 (1 GiB per array)" if n >= 1 << 26 else
+                   "input restored by a copy before each step", "parallelism": f"replicas x{world}",
+                   "plan": info},
+        "gpu_launches": info["launches"] * args.steps,
+        "clocks": clk.summary(),
+    }
+
+    design_bytes = info["hbm_passes"] * 2 * 4 * n
+    line["design_roofline"] = {
+        "hbm_passes": info["hbm_passes"], "design_bytes": design_bytes,
+        "roofline_ms": design_bytes / (hbm_gbs * 1e9) * 1e3,
+        "frac": (design_bytes / (hbm_gbs * 1e9) * 1e3) / ms_per_step,
+        "lower_bound_ms_8n": 8 * n / (hbm_gbs * 1e9) * 1e3,
+        "peak_gbs": hbm_gbs, "peak_source": peak_src,
+    }
+
+    if not args.no_extras and rank == 0:
+        # per-kernel times over K instrumented steps (plain launches, events
+        # between launches) for the roofline of the dominant kernel
+        L = info["launches"]
+        per_kind = {}
+        for i in range(args.steps):
+            buf.copy_(pristine)
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(L + 1)]
+            kinds = bt.sort_profiled_(buf, evs)
+            torch.cuda.synchronize()
+            for j in range(L):
+                per_kind.setdefault(kinds[j], []).append(evs[j].elapsed_time(evs[j + 1]))
+        tot = {k: sum(v) for k, v in per_kind.items()}
+        dom = max(tot, key=tot.get)
+        avg_ms = statistics.mean(per_kind[dom])
+        algo_bytes = 2 * 4 * n  # each launch reads and writes every key once
+        achieved = algo_bytes / (avg_ms / 1e3) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
+                            "frac": achieved / hbm_gbs, "traffic": None,
+                            "kernel": bt.KIND_NAMES[dom], "launches_per_step": len(per_kind[dom]) // args.steps,
+                            "avg_launch_ms": avg_ms, "peak_source": peak_src,
+                            "share": {bt.KIND_NAMES[k]: v / sum(tot.values()) for k, v in tot.items()}}
+
+        # end to end through the C ABI: pinned host keys -> device -> sort -> host
+        host_in = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        dev = torch.empty_like(pristine)
+        e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for i in range(args.steps + 1):
+            if i:
+                e_s[i - 1].record(stream)
+            dev.copy_(host_in, non_blocking=True)
+            bt.sort_(dev)
+            host_out.copy_(dev, non_blocking=True)
+            if i:
+                e_e[i - 1].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)) / args.steps
+        line["e2e"] = {"value": n / (e2e_ms / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
+                       "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms}
+        out = host_out.numpy().view(np.uint32)
+        assert np.all(out[1:] >= out[:-1])
+    if not args.no_cpu_baseline and rank == 0:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

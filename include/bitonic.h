@@ -1,0 +1,182 @@
+/*
+ * bitonic.h -- C ABI of the GB300 (sm_103a) bitonic sorting library.
+ *
+ * The library sorts 32-bit unsigned keys, and key/value pairs, with Batcher's
+ * bitonic sorting network as described in "The implementation and
+ * optimization of Bitonic sort algorithm based on CUDA" (Mu, Cui, Song;
+ * arXiv 1506.01446):
+ *   Section 3.1  the network: for n = 2^k, k phases; phase r merges 2^(k-r)
+ *                subsequences of length 2^r, each merge taking r half-cleaner
+ *                steps of n/2 compare-exchanges;
+ *   Section 3.2  k(k+1)/2 steps and n k (k+1) / 4 compare-exchanges in all;
+ *   Section 3.3  one kernel per step;
+ *   Section 4.1  steps whose subsequences fit in one block's shared memory
+ *                are fused into one kernel;
+ *   Section 4.2  a thread keeps several elements in registers and applies
+ *                successive steps to them without touching global memory.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named keys / vals / offsets are DEVICE pointers owned by the
+ *     caller; they must be at least 4-byte aligned.  Sorting is in place.
+ *   - Work is enqueued on `stream` (NULL = the legacy default stream) and the
+ *     call returns without waiting.  Argument errors are reported before
+ *     anything is enqueued; CUDA launch errors as BITONIC_ERR_CUDA.
+ *   - Device-side failures (a bounded wait that ran out) are written to a
+ *     device status word and reported by bitonic_last_device_error().
+ *   - n <= 1 (or nseg == 0) returns BITONIC_OK without launching anything.
+ *   - n > 2^31 returns BITONIC_ERR_UNSUPPORTED (indices are 32-bit).
+ *   - Sizes that are not powers of two are padded virtually to
+ *     N = next_pow2(n): positions >= n behave as keys that sort after every
+ *     real key (0xFFFFFFFF ascending); they are never read or written.
+ *   - The library owns a per-(device, stream) workspace (pair composites,
+ *     work lists, the status word) that grows on demand with cudaMalloc and
+ *     is freed by bitonic_release_workspace().  Calls on different streams
+ *     may run concurrently from different host threads; calls on one stream
+ *     are serialised by the caller.
+ *   - When `stream` is being captured into a CUDA graph, kernels are launched
+ *     straight into the capture; otherwise the library replays a cached CUDA
+ *     graph of the launch sequence (keyed by size, direction, kind and
+ *     buffers).
+ */
+#ifndef BITONIC_H
+#define BITONIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *bitonic_stream_t;
+/* Same type as cudaEvent_t. */
+typedef struct CUevent_st *bitonic_event_t;
+
+typedef enum {
+    BITONIC_OK = 0,
+    BITONIC_ERR_INVALID = 1,     /* null pointer, bad flag, negative count, bad alignment */
+    BITONIC_ERR_CUDA = 2,        /* a CUDA runtime call failed; see bitonic_last_error_message */
+    BITONIC_ERR_OOM = 3,         /* workspace could not be allocated */
+    BITONIC_ERR_TIMEOUT = 4,     /* a device-side bounded wait gave up */
+    BITONIC_ERR_UNSUPPORTED = 5  /* size beyond the supported range */
+} bitonic_status;
+
+/*
+ * Sorts keys[0..n) in place, ascending (ascending != 0) or descending.
+ * Section 3.1 network (bitonic build + bitonic merge, Section 3.2 work).
+ * The output is the unique sorted permutation of the input.
+ */
+bitonic_status bitonic_sort_u32(uint32_t *keys, size_t n, int ascending, bitonic_stream_t stream);
+
+/*
+ * Sorts key/value pairs in place.  Keys compare first; equal keys keep their
+ * original index order (ascending index in both directions), so the result is
+ * unique.  vals[i] travels with keys[i].  Uses a workspace of 8 * N bytes
+ * (one 64-bit composite (key', index) per element, key' = key or ~key) plus
+ * 4 * n bytes for the value gather.  The network is Section 3.1's, run on the
+ * composites.
+ */
+bitonic_status bitonic_sort_pairs_u32(uint32_t *keys, uint32_t *vals, size_t n, int ascending,
+                                      bitonic_stream_t stream);
+
+/*
+ * Sorts each segment keys[offsets[s] .. offsets[s+1]) ascending, for
+ * s = 0..nseg-1, in one batched launch sequence.  `offsets` is a device array
+ * of nseg + 1 non-decreasing int32 values (offsets[0] need not be 0); empty
+ * segments are allowed.  Offsets are device-resident and are not validated
+ * unless the environment variable BITONIC_DEBUG_CHECKS=1 is set, in which
+ * case a violation is reported as BITONIC_ERR_INVALID by
+ * bitonic_last_device_error().  Segments longer than the on-chip tile are
+ * sorted with additional merge passes; to plan those passes the call reads a
+ * 64-entry size histogram back to the host (one stream synchronisation) when
+ * at least one segment exceeds the tile.
+ */
+bitonic_status bitonic_sort_segmented_u32(uint32_t *keys, const int32_t *offsets, int nseg,
+                                          bitonic_stream_t stream);
+
+/* Segmented key/value sort: each segment sorted ascending by (key, index)
+ * with its values, as bitonic_sort_pairs_u32 does for one array. */
+bitonic_status bitonic_sort_segmented_pairs_u32(uint32_t *keys, uint32_t *vals,
+                                                const int32_t *offsets, int nseg,
+                                                bitonic_stream_t stream);
+
+/* Human-readable name of a status code (static storage). */
+const char *bitonic_status_string(bitonic_status s);
+
+/* Text of the last CUDA error seen by this host thread ("" if none). */
+const char *bitonic_last_error_message(void);
+
+/*
+ * Synchronises `stream`, reads and clears its device status word, and
+ * returns BITONIC_OK, BITONIC_ERR_TIMEOUT or BITONIC_ERR_INVALID (debug
+ * offset checks).  A stream that never ran a sort returns BITONIC_OK.
+ */
+bitonic_status bitonic_last_device_error(bitonic_stream_t stream);
+
+/* Frees every workspace and cached CUDA graph of the current device. */
+bitonic_status bitonic_release_workspace(void);
+
+/* ---- planning, tuning and instrumentation (no paper counterpart) -------- */
+
+/* Kernel variants, matching the three GPU columns of Section 5, Table 1. */
+typedef enum {
+    BITONIC_VARIANT_OPTIMIZED = 0, /* registers + shared memory + multi-stride global passes */
+    BITONIC_VARIANT_BASIC = 1,     /* Section 3.3: one kernel per step, one compare-exchange
+                                      per thread */
+    BITONIC_VARIANT_SEMI = 2       /* Section 4.1: shared-memory tile fusion, one stride per
+                                      global pass */
+} bitonic_variant;
+
+typedef struct {
+    int variant;          /* bitonic_variant */
+    int tile_log2;        /* log2 of keys per on-chip tile; 0 = automatic */
+    int global_bits;      /* strides fused per global pass; 0 = automatic */
+    int use_graph;        /* 1 = replay cached CUDA graphs (default), 0 = plain launches */
+} bitonic_options;
+
+/* Process-wide options (defaults: all zero except use_graph = 1). */
+bitonic_status bitonic_set_options(const bitonic_options *opt);
+bitonic_status bitonic_get_options(bitonic_options *opt);
+
+/*
+ * Describes the launch sequence bitonic_sort_u32 (pairs != 0: the composite
+ * sort of bitonic_sort_pairs_u32) would run for n under the current options:
+ * *launches = kernel launches, *hbm_passes = passes that read and write every
+ * key once (the design's memory traffic is hbm_passes * 2 * N * key bytes),
+ * *fused_steps and *global_steps = network steps done on chip / in global
+ * passes.  Any output pointer may be NULL.
+ */
+bitonic_status bitonic_plan_info(size_t n, int pairs, int *launches, int *hbm_passes,
+                                 int *fused_steps, int *global_steps);
+
+/*
+ * Same as bitonic_sort_u32 but launched without a graph, recording
+ * events[i] on `stream` before launch i of the sequence and events[L] after
+ * the last one (L = launches of bitonic_plan_info).  nevents must be >= L + 1.
+ * kinds (may be NULL, >= L entries) receives each launch's kernel kind:
+ * 0 = tile sort, 1 = global multi-stride pass, 2 = tile merge, 3 = single
+ * step (basic variant).
+ */
+bitonic_status bitonic_sort_u32_profiled(uint32_t *keys, size_t n, int ascending,
+                                         bitonic_stream_t stream, bitonic_event_t *events,
+                                         int nevents, int *kinds);
+
+/*
+ * Copies the launch plan of an n-key sort (key_bytes 4: keys, 8: pair
+ * composites) under the current options, for inspection and host-side
+ * tests.  info (max_info ints) receives N, the tile configuration id, its
+ * log2 keys per thread and log2 threads per CTA, the launch count L and the
+ * descriptor count D, then 7 ints per launch (kind, phase, hi, lo, flip,
+ * descriptor index, grid).  descs receives D descriptors of
+ * bitonic_debug_desc_size() bytes each (may be NULL).  Launches nothing.
+ */
+bitonic_status bitonic_debug_plan(size_t n, int key_bytes, int *info, int max_info, void *descs,
+                                  int max_descs);
+size_t bitonic_debug_desc_size(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BITONIC_H */

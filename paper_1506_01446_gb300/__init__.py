@@ -1,0 +1,199 @@
+"""GB300 (sm_103a) bitonic sorting library -- Python binding.
+
+Thin ctypes shims over the C ABI declared in ``include/bitonic.h``: argument
+marshalling only, every step of a sort runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams.  There is no CPU fallback: if the
+CUDA library is missing, :func:`load` raises.
+
+The sort is Batcher's bitonic network as described by Mu, Cui and Song,
+"The implementation and optimization of Bitonic sort algorithm based on CUDA"
+(Section 3.1 network, Section 3.3 one kernel per step, Section 4.1 shared
+memory, Section 4.2 registers).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libbitonic.so")
+
+OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED = range(6)
+VARIANT_OPTIMIZED, VARIANT_BASIC, VARIANT_SEMI = 0, 1, 2
+KIND_NAMES = {0: "tile_sort", 1: "global_pass", 2: "tile_merge", 3: "step"}
+
+# Every symbol include/bitonic.h declares.
+EXPORTS = (
+    "bitonic_sort_u32", "bitonic_sort_pairs_u32", "bitonic_sort_segmented_u32",
+    "bitonic_sort_segmented_pairs_u32", "bitonic_status_string", "bitonic_last_error_message",
+    "bitonic_last_device_error", "bitonic_release_workspace", "bitonic_set_options",
+    "bitonic_get_options", "bitonic_plan_info", "bitonic_sort_u32_profiled", "bitonic_debug_plan",
+    "bitonic_debug_desc_size",
+)
+
+
+class BitonicError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} {last_error_message()}".rstrip())
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("tile_log2", ctypes.c_int),
+                ("global_bits", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Loads libbitonic.so (built by ``paper_1506_01446_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, sz, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+    pint = ctypes.POINTER(ctypes.c_int)
+    lib.bitonic_sort_u32.argtypes = [vp, sz, i32, vp]
+    lib.bitonic_sort_pairs_u32.argtypes = [vp, vp, sz, i32, vp]
+    lib.bitonic_sort_segmented_u32.argtypes = [vp, vp, i32, vp]
+    lib.bitonic_sort_segmented_pairs_u32.argtypes = [vp, vp, vp, i32, vp]
+    lib.bitonic_status_string.argtypes = [i32]
+    lib.bitonic_status_string.restype = ctypes.c_char_p
+    lib.bitonic_last_error_message.argtypes = []
+    lib.bitonic_last_error_message.restype = ctypes.c_char_p
+    lib.bitonic_last_device_error.argtypes = [vp]
+    lib.bitonic_release_workspace.argtypes = []
+    lib.bitonic_set_options.argtypes = [ctypes.POINTER(Options)]
+    lib.bitonic_get_options.argtypes = [ctypes.POINTER(Options)]
+    lib.bitonic_plan_info.argtypes = [sz, i32, pint, pint, pint, pint]
+    lib.bitonic_sort_u32_profiled.argtypes = [vp, sz, i32, vp, ctypes.POINTER(vp), i32, pint]
+    lib.bitonic_debug_plan.argtypes = [sz, i32, pint, i32, vp, i32]
+    lib.bitonic_debug_desc_size.argtypes = []
+    lib.bitonic_debug_desc_size.restype = sz
+    for name in EXPORTS:
+        f = getattr(lib, name)
+        if f.restype is ctypes.c_int or f.restype is None:
+            pass
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().bitonic_status_string(int(status)).decode()
+
+
+def last_error_message() -> str:
+    return load().bitonic_last_error_message().decode()
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise BitonicError(status, what)
+
+
+def _stream_handle(stream):
+    """cudaStream_t of a torch stream (None = torch's current stream)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _u32_ptr(t, name):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.element_size() != 4:
+        raise ValueError(f"{name} must have 4-byte elements (uint32 or int32 view)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def sort_(keys, ascending: bool = True, stream=None):
+    """Sorts a CUDA tensor of 32-bit keys in place (unsigned order)."""
+    _check(load().bitonic_sort_u32(_u32_ptr(keys, "keys"), keys.numel(), int(bool(ascending)),
+                                   _stream_handle(stream)), "bitonic_sort_u32")
+    return keys
+
+
+def sort_pairs_(keys, vals, ascending: bool = True, stream=None):
+    """Sorts key/value pairs in place; equal keys keep their original order."""
+    if keys.numel() != vals.numel():
+        raise ValueError("keys and vals differ in length")
+    _check(load().bitonic_sort_pairs_u32(_u32_ptr(keys, "keys"), _u32_ptr(vals, "vals"), keys.numel(),
+                                         int(bool(ascending)), _stream_handle(stream)),
+           "bitonic_sort_pairs_u32")
+    return keys, vals
+
+
+def _offsets_ptr(offsets):
+    import torch
+    if not offsets.is_cuda or offsets.dtype != torch.int32 or not offsets.is_contiguous():
+        raise ValueError("offsets must be a contiguous int32 CUDA tensor")
+    return offsets.data_ptr()
+
+
+def sort_segmented_(keys, offsets, stream=None):
+    """Sorts keys[offsets[s]:offsets[s+1]] ascending for every segment s."""
+    nseg = offsets.numel() - 1
+    _check(load().bitonic_sort_segmented_u32(_u32_ptr(keys, "keys"), _offsets_ptr(offsets), nseg,
+                                             _stream_handle(stream)), "bitonic_sort_segmented_u32")
+    return keys
+
+
+def sort_segmented_pairs_(keys, vals, offsets, stream=None):
+    nseg = offsets.numel() - 1
+    _check(load().bitonic_sort_segmented_pairs_u32(_u32_ptr(keys, "keys"), _u32_ptr(vals, "vals"),
+                                                   _offsets_ptr(offsets), nseg, _stream_handle(stream)),
+           "bitonic_sort_segmented_pairs_u32")
+    return keys, vals
+
+
+def last_device_error(stream=None) -> int:
+    """Synchronises the stream and returns (and clears) its device status."""
+    return load().bitonic_last_device_error(_stream_handle(stream))
+
+
+def release_workspace():
+    _check(load().bitonic_release_workspace(), "bitonic_release_workspace")
+
+
+def get_options() -> dict:
+    o = Options()
+    _check(load().bitonic_get_options(ctypes.byref(o)), "bitonic_get_options")
+    return {f: getattr(o, f) for f, _ in Options._fields_}
+
+
+def set_options(variant=None, tile_log2=None, global_bits=None, use_graph=None):
+    cur = get_options()
+    for k, v in (("variant", variant), ("tile_log2", tile_log2), ("global_bits", global_bits),
+                 ("use_graph", use_graph)):
+        if v is not None:
+            cur[k] = int(v)
+    _check(load().bitonic_set_options(ctypes.byref(Options(**cur))), "bitonic_set_options")
+    return cur
+
+
+def plan_info(n: int, pairs: bool = False) -> dict:
+    out = [ctypes.c_int() for _ in range(4)]
+    _check(load().bitonic_plan_info(int(n), int(bool(pairs)), *[ctypes.byref(x) for x in out]),
+           "bitonic_plan_info")
+    return dict(zip(("launches", "hbm_passes", "fused_steps", "global_steps"), (x.value for x in out)))
+
+
+def sort_profiled_(keys, events, ascending: bool = True, stream=None):
+    """Like sort_ but without a graph, recording events[i] before launch i and
+    events[L] after the last; returns the kernel kind of each launch."""
+    n_ev = len(events)
+    arr = (ctypes.c_void_p * n_ev)(*[e.cuda_event for e in events])
+    kinds = (ctypes.c_int * n_ev)()
+    _check(load().bitonic_sort_u32_profiled(_u32_ptr(keys, "keys"), keys.numel(), int(bool(ascending)),
+                                            _stream_handle(stream), arr, n_ev, kinds),
+           "bitonic_sort_u32_profiled")
+    return list(kinds)

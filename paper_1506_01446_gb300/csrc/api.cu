@@ -1,0 +1,512 @@
+// C ABI of the library: argument checks, per-stream workspaces, plan and
+// CUDA-graph caches, and the launch sequences of each entry point.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "bitonic.h"
+#include "internal.h"
+#include "kernel_cfg.h"
+#include "seg.h"
+
+namespace bitonic {
+namespace {
+
+thread_local std::string t_last_error;
+
+// Device status word values.
+constexpr int kDevOk = 0;
+constexpr int kDevBadOffsets = 1;
+constexpr int kDevTimeout = 2;
+
+constexpr size_t kMaxGraphs = 64;
+constexpr uint64_t kMaxKeys = uint64_t(1) << 31;
+
+std::mutex g_mu;  // guards every piece of state below
+Options g_opt;
+
+struct StreamWs {
+    int* dev = nullptr;          // [0] status word, [1] work counter, [2..4] segment stats
+    int* host = nullptr;         // pinned copy of the stats
+    uint64_t* comp = nullptr;    // pair composites
+    size_t comp_cap = 0;         // in elements
+};
+
+struct PlanEntry {
+    Plan plan;
+    TileParams* d_descs = nullptr;
+};
+
+using PlanKey = std::tuple<uint64_t, int, int, int, int>;
+// op, n, ascending, ptr a, ptr b, ptr c, count, stream, variant, tile, gbits
+using GraphKey = std::tuple<int, uint64_t, int, uintptr_t, uintptr_t, uintptr_t, int, uintptr_t, int, int, int>;
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t stamp = 0;
+};
+
+struct DeviceState {
+    bool inited = false;
+    cudaStream_t capture = nullptr;
+    int num_sms = 0;
+    std::map<cudaStream_t, StreamWs> ws;
+    std::map<PlanKey, std::unique_ptr<PlanEntry>> plans;
+    std::map<GraphKey, GraphEntry> graphs;
+    uint64_t clock = 0;
+};
+
+std::map<int, DeviceState> g_dev;
+
+int debug_checks()
+{
+    static int v = [] {
+        const char* e = std::getenv("BITONIC_DEBUG_CHECKS");
+        return (e && e[0] == '1') ? 1 : 0;
+    }();
+    return v;
+}
+
+bitonic_status cuda_fail(cudaError_t e, const char* what)
+{
+    t_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();  // clear a sticky launch error
+    return e == cudaErrorMemoryAllocation ? BITONIC_ERR_OOM : BITONIC_ERR_CUDA;
+}
+
+#define BT_CK(call)                                      \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+bitonic_status device_state(DeviceState** out)
+{
+    int dev = 0;
+    BT_CK(cudaGetDevice(&dev));
+    DeviceState& ds = g_dev[dev];
+    if (!ds.inited) {
+        BT_CK(cudaDeviceGetAttribute(&ds.num_sms, cudaDevAttrMultiProcessorCount, dev));
+        BT_CK(init_tile_attributes());
+        BT_CK(seg_init_attributes());
+        BT_CK(cudaStreamCreateWithFlags(&ds.capture, cudaStreamNonBlocking));
+        ds.inited = true;
+    }
+    *out = &ds;
+    return BITONIC_OK;
+}
+
+bitonic_status stream_ws(DeviceState& ds, cudaStream_t s, size_t comp_need, StreamWs** out)
+{
+    StreamWs& w = ds.ws[s];
+    if (!w.dev) {
+        BT_CK(cudaMalloc(&w.dev, 8 * sizeof(int)));
+        BT_CK(cudaMemset(w.dev, 0, 8 * sizeof(int)));
+        BT_CK(cudaMallocHost(&w.host, 8 * sizeof(int)));
+    }
+    if (comp_need > w.comp_cap) {
+        if (w.comp) {
+            BT_CK(cudaStreamSynchronize(s));
+            BT_CK(cudaFree(w.comp));
+            w.comp = nullptr;
+            w.comp_cap = 0;
+            // graphs captured with the old buffer must not be replayed
+            for (auto it = ds.graphs.begin(); it != ds.graphs.end();) {
+                if (std::get<7>(it->first) == (uintptr_t)s) {
+                    cudaGraphExecDestroy(it->second.exec);
+                    it = ds.graphs.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        size_t cap = (comp_need + 1) & ~size_t(1);
+        BT_CK(cudaMalloc(&w.comp, cap * sizeof(uint64_t)));
+        w.comp_cap = cap;
+    }
+    *out = &w;
+    return BITONIC_OK;
+}
+
+bitonic_status get_plan(DeviceState& ds, uint64_t nv, int key_bytes, PlanEntry** out)
+{
+    uint64_t N = 2;
+    while (N < nv) N <<= 1;
+    PlanKey key{N, key_bytes, g_opt.variant, g_opt.tile_log2, g_opt.global_bits};
+    auto it = ds.plans.find(key);
+    if (it == ds.plans.end()) {
+        auto pe = std::make_unique<PlanEntry>();
+        pe->plan = make_plan(N, key_bytes, g_opt);
+        if (!pe->plan.ok) {
+            t_last_error = "planner could not schedule this size";
+            return BITONIC_ERR_UNSUPPORTED;
+        }
+        if (!pe->plan.descs.empty()) {
+            const size_t bytes = pe->plan.descs.size() * sizeof(TileParams);
+            BT_CK(cudaMalloc(&pe->d_descs, bytes));
+            BT_CK(cudaMemcpy(pe->d_descs, pe->plan.descs.data(), bytes, cudaMemcpyHostToDevice));
+        }
+        it = ds.plans.emplace(key, std::move(pe)).first;
+    }
+    *out = it->second.get();
+    return BITONIC_OK;
+}
+
+// Enqueues the plan's launches on `s`.  events / kinds are optional.
+bitonic_status enqueue_plan(const PlanEntry& pe, void* base, uint32_t lo, uint32_t hi, int desc,
+                            int key_bytes, cudaStream_t s, cudaEvent_t* events, int* kinds)
+{
+    const Plan& pl = pe.plan;
+    for (size_t i = 0; i < pl.launches.size(); ++i) {
+        const Launch& L = pl.launches[i];
+        if (events) BT_CK(cudaEventRecord(events[i], s));
+        if (kinds) kinds[i] = L.kind;
+        cudaError_t e;
+        if (L.kind == KIND_STEP)
+            e = launch_step(key_bytes, desc, base, lo, hi, (uint32_t)pl.N, L.hi, L.flip, s);
+        else
+            e = launch_tile(pl.cfg, desc, base, lo, hi, pe.d_descs + L.desc, L.grid, s);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    }
+    if (events) BT_CK(cudaEventRecord(events[pl.launches.size()], s));
+    return BITONIC_OK;
+}
+
+template <class F>
+bitonic_status run_graphed(DeviceState& ds, const GraphKey& key, cudaStream_t user, F&& enqueue)
+{
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    BT_CK(cudaStreamIsCapturing(user, &cst));
+    if (!g_opt.use_graph || cst != cudaStreamCaptureStatusNone) return enqueue(user);
+    auto it = ds.graphs.find(key);
+    if (it == ds.graphs.end()) {
+        BT_CK(cudaStreamBeginCapture(ds.capture, cudaStreamCaptureModeThreadLocal));
+        bitonic_status st = enqueue(ds.capture);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ds.capture, &g);
+        if (st != BITONIC_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        if (ds.graphs.size() >= kMaxGraphs) {
+            auto victim = ds.graphs.begin();
+            for (auto jt = ds.graphs.begin(); jt != ds.graphs.end(); ++jt)
+                if (jt->second.stamp < victim->second.stamp) victim = jt;
+            BT_CK(cudaDeviceSynchronize());
+            cudaGraphExecDestroy(victim->second.exec);
+            ds.graphs.erase(victim);
+        }
+        it = ds.graphs.emplace(key, GraphEntry{ex, 0}).first;
+    }
+    it->second.stamp = ++ds.clock;
+    BT_CK(cudaGraphLaunch(it->second.exec, user));
+    return BITONIC_OK;
+}
+
+bitonic_status check_keys_ptr(const void* p)
+{
+    if (!p || ((uintptr_t)p & 3u)) {
+        t_last_error = "null or misaligned pointer";
+        return BITONIC_ERR_INVALID;
+    }
+    return BITONIC_OK;
+}
+
+bitonic_status sort_u32_impl(uint32_t* keys, size_t n, int ascending, cudaStream_t s, cudaEvent_t* events,
+                             int nevents, int* kinds)
+{
+    if (n > kMaxKeys) return BITONIC_ERR_UNSUPPORTED;
+    if (n <= 1) return BITONIC_OK;
+    bitonic_status st = check_keys_ptr(keys);
+    if (st) return st;
+    const uint32_t front = (uint32_t)(((uintptr_t)keys & 15u) / 4u);
+    const uint64_t nv = (uint64_t)n + front;
+    if (nv > kMaxKeys) return BITONIC_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> g(g_mu);
+    DeviceState* ds;
+    if ((st = device_state(&ds))) return st;
+    PlanEntry* pe;
+    if ((st = get_plan(*ds, nv, 4, &pe))) return st;
+    uint32_t* base = keys - front;
+    const int desc = ascending ? 0 : 1;
+    if (events) {
+        if (nevents < (int)pe->plan.launches.size() + 1) return BITONIC_ERR_INVALID;
+        return enqueue_plan(*pe, base, front, (uint32_t)nv, desc, 4, s, events, kinds);
+    }
+    GraphKey key{0, n, desc, (uintptr_t)keys, 0, 0, 0, 0, g_opt.variant, g_opt.tile_log2, g_opt.global_bits};
+    return run_graphed(*ds, key, s, [&](cudaStream_t cs) {
+        return enqueue_plan(*pe, base, front, (uint32_t)nv, desc, 4, cs, nullptr, nullptr);
+    });
+}
+
+bitonic_status sort_pairs_impl(uint32_t* keys, uint32_t* vals, size_t n, int ascending, cudaStream_t s)
+{
+    if (n > kMaxKeys) return BITONIC_ERR_UNSUPPORTED;
+    if (n <= 1) return BITONIC_OK;
+    bitonic_status st = check_keys_ptr(keys);
+    if (st || (st = check_keys_ptr(vals))) return st;
+    std::lock_guard<std::mutex> g(g_mu);
+    DeviceState* ds;
+    if ((st = device_state(&ds))) return st;
+    StreamWs* w;
+    if ((st = stream_ws(*ds, s, n, &w))) return st;
+    PlanEntry* pe;
+    if ((st = get_plan(*ds, n, 8, &pe))) return st;
+    const int desc = ascending ? 0 : 1;
+    const uint32_t nn = (uint32_t)n;
+    uint64_t* comp = w->comp;
+    GraphKey key{1, n, desc, (uintptr_t)keys, (uintptr_t)vals, (uintptr_t)comp, 0, (uintptr_t)s, g_opt.variant,
+                 g_opt.tile_log2, g_opt.global_bits};
+    return run_graphed(*ds, key, s, [&](cudaStream_t cs) -> bitonic_status {
+        BT_CK(launch_pairs_pack(comp, keys, nn, desc, cs));
+        bitonic_status st2 = enqueue_plan(*pe, comp, 0, nn, 0, 8, cs, nullptr, nullptr);
+        if (st2) return st2;
+        BT_CK(launch_pairs_gather(comp, vals, nn, cs));
+        BT_CK(launch_pairs_unpack(comp, keys, vals, nn, desc, cs));
+        return BITONIC_OK;
+    });
+}
+
+int seg_grid(const DeviceState& ds, int nseg)
+{
+    int g = ds.num_sms * 8;
+    return nseg < g ? nseg : g;
+}
+
+bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t* offsets, int nseg,
+                                   cudaStream_t s)
+{
+    if (nseg < 0 || !offsets) {
+        t_last_error = "negative segment count or null offsets";
+        return BITONIC_ERR_INVALID;
+    }
+    if (nseg == 0) return BITONIC_OK;
+    bitonic_status st = check_keys_ptr(keys);
+    if (st) return st;
+    if (vals && (st = check_keys_ptr(vals))) return st;
+    if ((uintptr_t)offsets & 3u) return BITONIC_ERR_INVALID;
+    std::lock_guard<std::mutex> g(g_mu);
+    DeviceState* ds;
+    if ((st = device_state(&ds))) return st;
+    StreamWs* w;
+    if ((st = stream_ws(*ds, s, 0, &w))) return st;
+    const int grid = seg_grid(*ds, nseg);
+    if (!vals) {
+        int* counter = w->dev + 1;
+        int* status = w->dev;
+        GraphKey key{2, 0, 1, (uintptr_t)keys, 0, (uintptr_t)offsets, nseg, (uintptr_t)s, 0, 0, 0};
+        return run_graphed(*ds, key, s, [&](cudaStream_t cs) -> bitonic_status {
+            BT_CK(seg_launch_keys(keys, offsets, nseg, counter, status, debug_checks(), grid, cs));
+            return BITONIC_OK;
+        });
+    }
+    // Pairs: longer segments need a composite workspace sized by the span.
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    BT_CK(cudaStreamIsCapturing(s, &cst));
+    if (cst != cudaStreamCaptureStatusNone) {
+        t_last_error = "segmented pair sort reads its segment sizes back and cannot be captured";
+        return BITONIC_ERR_UNSUPPORTED;
+    }
+    BT_CK(seg_launch_stats(offsets, nseg, w->dev + 2, s));
+    BT_CK(cudaMemcpyAsync(w->host, w->dev + 2, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BT_CK(cudaStreamSynchronize(s));
+    const int32_t first = w->host[0], last = w->host[1], longest = w->host[2];
+    size_t need = 0;
+    if ((uint32_t)longest > kSegSmemPairs && last > first) need = (size_t)(last - first);
+    if ((st = stream_ws(*ds, s, need, &w))) return st;
+    BT_CK(seg_launch_pairs(keys, vals, offsets, nseg, w->comp, first, w->dev + 1, w->dev, debug_checks(), grid, s));
+    return BITONIC_OK;
+}
+
+}  // namespace
+
+Options current_options()
+{
+    std::lock_guard<std::mutex> g(g_mu);
+    return g_opt;
+}
+
+}  // namespace bitonic
+
+using namespace bitonic;
+
+extern "C" {
+
+bitonic_status bitonic_sort_u32(uint32_t* keys, size_t n, int ascending, bitonic_stream_t stream)
+{
+    return sort_u32_impl(keys, n, ascending, (cudaStream_t)stream, nullptr, 0, nullptr);
+}
+
+bitonic_status bitonic_sort_pairs_u32(uint32_t* keys, uint32_t* vals, size_t n, int ascending,
+                                      bitonic_stream_t stream)
+{
+    return sort_pairs_impl(keys, vals, n, ascending, (cudaStream_t)stream);
+}
+
+bitonic_status bitonic_sort_segmented_u32(uint32_t* keys, const int32_t* offsets, int nseg,
+                                          bitonic_stream_t stream)
+{
+    return sort_segmented_impl(keys, nullptr, offsets, nseg, (cudaStream_t)stream);
+}
+
+bitonic_status bitonic_sort_segmented_pairs_u32(uint32_t* keys, uint32_t* vals, const int32_t* offsets,
+                                                int nseg, bitonic_stream_t stream)
+{
+    if (!vals && nseg > 0) return BITONIC_ERR_INVALID;
+    return sort_segmented_impl(keys, vals, offsets, nseg, (cudaStream_t)stream);
+}
+
+const char* bitonic_status_string(bitonic_status s)
+{
+    switch (s) {
+        case BITONIC_OK: return "BITONIC_OK";
+        case BITONIC_ERR_INVALID: return "BITONIC_ERR_INVALID";
+        case BITONIC_ERR_CUDA: return "BITONIC_ERR_CUDA";
+        case BITONIC_ERR_OOM: return "BITONIC_ERR_OOM";
+        case BITONIC_ERR_TIMEOUT: return "BITONIC_ERR_TIMEOUT";
+        case BITONIC_ERR_UNSUPPORTED: return "BITONIC_ERR_UNSUPPORTED";
+    }
+    return "BITONIC_UNKNOWN_STATUS";
+}
+
+const char* bitonic_last_error_message(void) { return t_last_error.c_str(); }
+
+bitonic_status bitonic_last_device_error(bitonic_stream_t stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    BT_CK(cudaStreamSynchronize(s));
+    std::lock_guard<std::mutex> g(g_mu);
+    int dev = 0;
+    BT_CK(cudaGetDevice(&dev));
+    auto dit = g_dev.find(dev);
+    if (dit == g_dev.end()) return BITONIC_OK;
+    auto it = dit->second.ws.find(s);
+    if (it == dit->second.ws.end() || !it->second.dev) return BITONIC_OK;
+    int word = 0;
+    BT_CK(cudaMemcpy(&word, it->second.dev, sizeof(int), cudaMemcpyDeviceToHost));
+    BT_CK(cudaMemset(it->second.dev, 0, sizeof(int)));
+    if (word == kDevOk) return BITONIC_OK;
+    if (word == kDevBadOffsets) return BITONIC_ERR_INVALID;
+    if (word == kDevTimeout) return BITONIC_ERR_TIMEOUT;
+    return BITONIC_ERR_CUDA;
+}
+
+bitonic_status bitonic_release_workspace(void)
+{
+    std::lock_guard<std::mutex> g(g_mu);
+    int dev = 0;
+    BT_CK(cudaGetDevice(&dev));
+    auto dit = g_dev.find(dev);
+    if (dit == g_dev.end()) return BITONIC_OK;
+    DeviceState& ds = dit->second;
+    BT_CK(cudaDeviceSynchronize());
+    for (auto& kv : ds.graphs) cudaGraphExecDestroy(kv.second.exec);
+    ds.graphs.clear();
+    for (auto& kv : ds.plans)
+        if (kv.second->d_descs) cudaFree(kv.second->d_descs);
+    ds.plans.clear();
+    for (auto& kv : ds.ws) {
+        if (kv.second.dev) cudaFree(kv.second.dev);
+        if (kv.second.host) cudaFreeHost(kv.second.host);
+        if (kv.second.comp) cudaFree(kv.second.comp);
+    }
+    ds.ws.clear();
+    return BITONIC_OK;
+}
+
+bitonic_status bitonic_set_options(const bitonic_options* opt)
+{
+    if (!opt) return BITONIC_ERR_INVALID;
+    if (opt->variant < 0 || opt->variant > 2) return BITONIC_ERR_INVALID;
+    if (opt->tile_log2 != 0 && (opt->tile_log2 < 12 || opt->tile_log2 > 14)) return BITONIC_ERR_INVALID;
+    if (opt->global_bits < 0 || opt->global_bits > 16) return BITONIC_ERR_INVALID;
+    std::lock_guard<std::mutex> g(g_mu);
+    g_opt.variant = opt->variant;
+    g_opt.tile_log2 = opt->tile_log2;
+    g_opt.global_bits = opt->global_bits;
+    g_opt.use_graph = opt->use_graph ? 1 : 0;
+    return BITONIC_OK;
+}
+
+bitonic_status bitonic_get_options(bitonic_options* opt)
+{
+    if (!opt) return BITONIC_ERR_INVALID;
+    std::lock_guard<std::mutex> g(g_mu);
+    opt->variant = g_opt.variant;
+    opt->tile_log2 = g_opt.tile_log2;
+    opt->global_bits = g_opt.global_bits;
+    opt->use_graph = g_opt.use_graph;
+    return BITONIC_OK;
+}
+
+bitonic_status bitonic_plan_info(size_t n, int pairs, int* launches, int* hbm_passes, int* fused_steps,
+                                 int* global_steps)
+{
+    if (n > kMaxKeys) return BITONIC_ERR_UNSUPPORTED;
+    Options o = current_options();
+    if (n <= 1) {
+        if (launches) *launches = 0;
+        if (hbm_passes) *hbm_passes = 0;
+        if (fused_steps) *fused_steps = 0;
+        if (global_steps) *global_steps = 0;
+        return BITONIC_OK;
+    }
+    Plan p = make_plan(n, pairs ? 8 : 4, o);
+    if (!p.ok) return BITONIC_ERR_UNSUPPORTED;
+    if (launches) *launches = (int)p.launches.size() + (pairs ? 3 : 0);
+    if (hbm_passes) *hbm_passes = p.hbm_passes;
+    if (fused_steps) *fused_steps = p.fused_steps;
+    if (global_steps) *global_steps = p.global_steps;
+    return BITONIC_OK;
+}
+
+bitonic_status bitonic_sort_u32_profiled(uint32_t* keys, size_t n, int ascending, bitonic_stream_t stream,
+                                         bitonic_event_t* events, int nevents, int* kinds)
+{
+    if (!events) return BITONIC_ERR_INVALID;
+    return sort_u32_impl(keys, n, ascending, (cudaStream_t)stream, (cudaEvent_t*)events, nevents, kinds);
+}
+
+// Copies the plan of an n-key sort (key_bytes 4 or 8) for inspection:
+// info[0] = N, info[1] = cfg id, info[2] = log_r, info[3] = log_t,
+// info[4] = launches, info[5] = descriptors; then 7 ints per launch
+// (kind, phase, hi, lo, flip, desc, grid).  descs receives up to max_descs
+// TileParams.  Host-only: launches nothing.
+bitonic_status bitonic_debug_plan(size_t n, int key_bytes, int* info, int max_info, void* descs,
+                                  int max_descs)
+{
+    if (!info || max_info < 6 || (key_bytes != 4 && key_bytes != 8)) return BITONIC_ERR_INVALID;
+    Plan p = make_plan(n < 2 ? 2 : n, key_bytes, current_options());
+    if (!p.ok) return BITONIC_ERR_UNSUPPORTED;
+    info[0] = (int)p.N;
+    info[1] = p.cfg;
+    info[2] = p.cfg >= 0 ? tile_cfg(p.cfg).log_r : 0;
+    info[3] = p.cfg >= 0 ? tile_cfg(p.cfg).log_t : 0;
+    info[4] = (int)p.launches.size();
+    info[5] = (int)p.descs.size();
+    if (max_info < 6 + 7 * (int)p.launches.size() || max_descs < (int)p.descs.size()) return BITONIC_ERR_INVALID;
+    for (size_t i = 0; i < p.launches.size(); ++i) {
+        const Launch& L = p.launches[i];
+        int* o = info + 6 + 7 * i;
+        o[0] = L.kind; o[1] = L.phase; o[2] = L.hi; o[3] = L.lo; o[4] = L.flip; o[5] = L.desc; o[6] = (int)L.grid;
+    }
+    if (descs && !p.descs.empty()) std::memcpy(descs, p.descs.data(), p.descs.size() * sizeof(TileParams));
+    return BITONIC_OK;
+}
+
+size_t bitonic_debug_desc_size(void) { return sizeof(TileParams); }
+
+}  // extern "C"

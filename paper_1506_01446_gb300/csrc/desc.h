@@ -1,0 +1,55 @@
+// Launch descriptors shared by the host planner and the device tile engine.
+//
+// A tile pass works on a tile of 2^m keys.  Tile-local index L (m bits) maps
+// to a global (virtual) position g0 ^ G(L), where G is linear over GF(2):
+// G(L) = XOR of gvec[j] over the set bits j of L, and g0 is the CTA's base
+// (its block index scattered into the global bits that are not in the tile).
+// Local bits 0..c-1 map to global bits 0..c-1, so the tile is made of
+// aligned rows of 2^c consecutive keys.
+//
+// The network runs on local indices in the mirror form: the first step of a
+// phase pairs L with L ^ (2^(b+1) - 1) (b = the phase's top bit), the others
+// pair L with L ^ 2^b, and the lower index always receives the element that
+// sorts first.  A phase's first step that spans global bits outside the tile
+// is still a local mirror step: its top local bit maps to 2^(p-1) XOR the
+// global bits below p-1 that the tile leaves out.
+//
+// The steps are split into rounds.  In a round each thread holds R = 2^LOG_R
+// keys in registers: register-index bits 0..VB-1 are the components of one
+// 16-byte vector (local bits 0..VB-1), bits VB.. are "register bits" whose
+// local vectors are reg_loc[]; thread-index bit i has local vector thr_loc[i].
+// Between rounds the keys pass through shared memory (a transpose).
+#pragma once
+
+#include <stdint.h>
+
+namespace bitonic {
+
+constexpr int kMaxLogThreads = 10;
+constexpr int kMaxRegBits = 5;       // LOG_R - VB
+constexpr int kMaxRounds = 100;
+constexpr int kMaxStepsPerRound = 36;
+constexpr int kMaxLocalBits = 16;
+
+// Step code: register-index bit q in bits 0..3, kStepFlip set for a mirror step.
+constexpr uint8_t kStepFlip = 16;
+
+struct RoundDesc {
+    uint16_t thr_loc[kMaxLogThreads];  // local vector of thread-index bit i
+    uint16_t reg_loc[kMaxRegBits];     // local vector of register bit VB + j
+    uint8_t nsteps;
+    uint8_t steps[kMaxStepsPerRound];
+    uint8_t pad_[3];
+};
+
+struct TileParams {
+    uint32_t gvec[kMaxLocalBits];  // global vector of local bit j
+    uint8_t free_bits[32];         // global bit that receives bit i of the CTA index
+    uint8_t m;                     // local bits
+    uint8_t nfree;                 // CTA index bits
+    uint8_t contiguous;            // tile is one aligned block of 2^m positions
+    uint8_t nrounds;
+    RoundDesc rounds[kMaxRounds];
+};
+
+}  // namespace bitonic

@@ -1,0 +1,271 @@
+// Device side of the tile engine: the register network (Section 4.2), the
+// shared-memory transposes between rounds (Section 4.1) and the global
+// loads / stores with virtual padding.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "desc.h"
+
+namespace bitonic {
+
+template <typename K>
+struct KeyTraits;
+
+template <>
+struct KeyTraits<uint32_t> {
+    static constexpr int VEC = 4;  // keys per 16-byte vector
+    static constexpr int VB = 2;   // log2(VEC)
+    using Vec = uint4;
+    static constexpr uint32_t kMax = 0xFFFFFFFFu;
+};
+
+template <>
+struct KeyTraits<uint64_t> {
+    static constexpr int VEC = 2;
+    static constexpr int VB = 1;
+    using Vec = ulonglong2;
+    static constexpr uint64_t kMax = 0xFFFFFFFFFFFFFFFFull;
+};
+
+// Shared-memory swizzle on vector indices: the low 3 bits (the 16-byte bank
+// group within a 128-byte line) are XORed with every higher 3-bit group.
+// Linear over GF(2), so phys(a ^ b) = phys(a) ^ phys(b).  A quarter warp
+// whose 3 lane bits sit on local vector bits of distinct residue mod 3 hits 8
+// distinct bank groups.
+__device__ __forceinline__ uint32_t swz(uint32_t lv)
+{
+    uint32_t f = (lv >> 3) ^ (lv >> 6) ^ (lv >> 9) ^ (lv >> 12) ^ (lv >> 15);
+    return lv ^ (f & 7u);
+}
+
+// Compare-exchange: the lower register receives the key that sorts first.
+template <bool DESC, typename K>
+__device__ __forceinline__ void cmpx(K& a, K& b)
+{
+    K lo = a < b ? a : b;
+    K hi = a < b ? b : a;
+    a = DESC ? hi : lo;
+    b = DESC ? lo : hi;
+}
+
+// One network step on the register array.  FLIP: mirror step at register bit
+// Q (pairs i with i ^ (2^(Q+1) - 1)); otherwise half-cleaner (i with i ^ 2^Q).
+template <int Q, bool FLIP, bool DESC, typename K, int R>
+__device__ __forceinline__ void net_step(K (&r)[R])
+{
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        if (i & (1 << Q)) continue;
+        const int j = FLIP ? (i ^ ((2 << Q) - 1)) : (i | (1 << Q));
+        cmpx<DESC>(r[i], r[j]);
+    }
+}
+
+template <bool DESC, typename K, int R>
+__device__ __forceinline__ void run_step(K (&r)[R], int code)
+{
+    constexpr int LOG_R = (R >= 128) ? 7 : (R >= 64) ? 6 : (R >= 32) ? 5 : (R >= 16) ? 4 : (R >= 8) ? 3 : (R >= 4) ? 2 : 1;
+#define BITONIC_STEP_CASE(Q)                                                  \
+    case Q:                                                                   \
+        if constexpr (Q < LOG_R) net_step<Q, false, DESC>(r);                 \
+        break;                                                                \
+    case Q + kStepFlip:                                                       \
+        if constexpr (Q < LOG_R) net_step<Q, true, DESC>(r);                  \
+        break;
+    switch (code) {
+        BITONIC_STEP_CASE(0)
+        BITONIC_STEP_CASE(1)
+        BITONIC_STEP_CASE(2)
+        BITONIC_STEP_CASE(3)
+        BITONIC_STEP_CASE(4)
+        BITONIC_STEP_CASE(5)
+        BITONIC_STEP_CASE(6)
+        default: break;
+    }
+#undef BITONIC_STEP_CASE
+}
+
+template <bool DESC, typename K, int R>
+__device__ __forceinline__ void run_round_steps(K (&r)[R], const RoundDesc& rd)
+{
+    const int ns = rd.nsteps;
+    for (int s = 0; s < ns; ++s) run_step<DESC>(r, (int)rd.steps[s]);
+}
+
+// Thread part of a round's local index: XOR of thr_loc[i] over set bits i of x.
+template <int LOG_T>
+__device__ __forceinline__ uint32_t thread_local_index(const RoundDesc& rd, uint32_t x)
+{
+    uint32_t L = 0;
+#pragma unroll
+    for (int i = 0; i < LOG_T; ++i)
+        if ((x >> i) & 1u) L ^= rd.thr_loc[i];
+    return L;
+}
+
+// Register part of vector v's local index (v indexes the R / VEC vectors).
+template <int NREG>
+__device__ __forceinline__ uint32_t reg_local_index(const uint32_t (&rv)[NREG], int v)
+{
+    uint32_t L = 0;
+#pragma unroll
+    for (int j = 0; j < NREG; ++j)
+        if ((v >> j) & 1) L ^= rv[j];
+    return L;
+}
+
+// Global position of a local index: XOR of gvec over its set bits.
+__device__ __forceinline__ uint32_t global_of_local(const TileParams& P, uint32_t L)
+{
+    uint32_t g = 0;
+    const int m = P.m;
+    for (int j = 0; j < m; ++j)
+        if ((L >> j) & 1u) g ^= P.gvec[j];
+    return g;
+}
+
+__device__ __forceinline__ uint32_t cta_base(const TileParams& P, uint32_t cta)
+{
+    uint32_t g = 0;
+    const int nf = P.nfree;
+    for (int i = 0; i < nf; ++i)
+        if ((cta >> i) & 1u) g |= 1u << P.free_bits[i];
+    return g;
+}
+
+template <typename K>
+__device__ __forceinline__ void vec_to_regs(const typename KeyTraits<K>::Vec& w, K* r);
+
+template <>
+__device__ __forceinline__ void vec_to_regs<uint32_t>(const uint4& w, uint32_t* r)
+{
+    r[0] = w.x; r[1] = w.y; r[2] = w.z; r[3] = w.w;
+}
+
+template <>
+__device__ __forceinline__ void vec_to_regs<uint64_t>(const ulonglong2& w, uint64_t* r)
+{
+    r[0] = w.x; r[1] = w.y;
+}
+
+template <typename K>
+__device__ __forceinline__ typename KeyTraits<K>::Vec regs_to_vec(const K* r);
+
+template <>
+__device__ __forceinline__ uint4 regs_to_vec<uint32_t>(const uint32_t* r)
+{
+    return make_uint4(r[0], r[1], r[2], r[3]);
+}
+
+template <>
+__device__ __forceinline__ ulonglong2 regs_to_vec<uint64_t>(const uint64_t* r)
+{
+    return make_ulonglong2(r[0], r[1]);
+}
+
+// The tile engine for one CTA.  LOG_R keys-per-thread bits, LOG_T thread bits.
+template <typename K, bool DESC, int LOG_R, int LOG_T>
+struct Tile {
+    static constexpr int R = 1 << LOG_R;
+    static constexpr int VEC = KeyTraits<K>::VEC;
+    static constexpr int VB = KeyTraits<K>::VB;
+    static constexpr int NV = R / VEC;           // vectors per thread
+    static constexpr int NREG = LOG_R - VB;      // register bits beyond the vector
+    using Vec = typename KeyTraits<K>::Vec;
+    static_assert(NREG >= 1 && NREG <= kMaxRegBits, "register bits out of range");
+    static_assert(LOG_T <= kMaxLogThreads, "too many threads");
+
+    static constexpr K kFrontPad = DESC ? KeyTraits<K>::kMax : K(0);
+    static constexpr K kTailPad = DESC ? K(0) : KeyTraits<K>::kMax;
+
+    K r[R];
+
+    __device__ __forceinline__ void load_reg_vectors(const RoundDesc& rd, uint32_t (&rv)[NREG])
+    {
+#pragma unroll
+        for (int j = 0; j < NREG; ++j) rv[j] = rd.reg_loc[j];
+    }
+
+    // Global load of round rd's layout.  base points at virtual position 0;
+    // positions [lo, hi) hold real keys, others are pads.
+    __device__ __forceinline__ void load_global(const K* __restrict__ base, uint32_t lo, uint32_t hi,
+                                                const TileParams& P, const RoundDesc& rd, uint32_t g0,
+                                                uint32_t x)
+    {
+        uint32_t rv[NREG];
+        load_reg_vectors(rd, rv);
+        const uint32_t gt = g0 ^ global_of_local(P, thread_local_index<LOG_T>(rd, x));
+        uint32_t gr[NREG];
+#pragma unroll
+        for (int j = 0; j < NREG; ++j) gr[j] = global_of_local(P, rv[j]);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const uint32_t pos = gt ^ reg_local_index<NREG>(gr, v);
+            K* dst = r + v * VEC;
+            if (pos >= lo && pos + VEC <= hi) {
+                vec_to_regs<K>(*reinterpret_cast<const Vec*>(base + pos), dst);
+            } else {
+#pragma unroll
+                for (int c = 0; c < VEC; ++c) {
+                    const uint32_t p = pos + c;
+                    dst[c] = p < lo ? kFrontPad : (p >= hi ? kTailPad : base[p]);
+                }
+            }
+        }
+    }
+
+    __device__ __forceinline__ void store_global(K* __restrict__ base, uint32_t lo, uint32_t hi,
+                                                 const TileParams& P, const RoundDesc& rd, uint32_t g0,
+                                                 uint32_t x)
+    {
+        uint32_t rv[NREG];
+        load_reg_vectors(rd, rv);
+        const uint32_t gt = g0 ^ global_of_local(P, thread_local_index<LOG_T>(rd, x));
+        uint32_t gr[NREG];
+#pragma unroll
+        for (int j = 0; j < NREG; ++j) gr[j] = global_of_local(P, rv[j]);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const uint32_t pos = gt ^ reg_local_index<NREG>(gr, v);
+            const K* src = r + v * VEC;
+            if (pos >= lo && pos + VEC <= hi) {
+                *reinterpret_cast<Vec*>(base + pos) = regs_to_vec<K>(src);
+            } else if (pos + VEC > lo && pos < hi) {
+#pragma unroll
+                for (int c = 0; c < VEC; ++c) {
+                    const uint32_t p = pos + c;
+                    if (p >= lo && p < hi) base[p] = src[c];
+                }
+            }
+        }
+    }
+
+    // Shared-memory addresses (in vectors) of this thread's vectors under rd.
+    __device__ __forceinline__ void smem_write(Vec* sm, const RoundDesc& rd, uint32_t x)
+    {
+        uint32_t rv[NREG];
+        load_reg_vectors(rd, rv);
+        uint32_t pr[NREG];
+#pragma unroll
+        for (int j = 0; j < NREG; ++j) pr[j] = swz(rv[j] >> VB);
+        const uint32_t pt = swz(thread_local_index<LOG_T>(rd, x) >> VB);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sm[pt ^ reg_local_index<NREG>(pr, v)] = regs_to_vec<K>(r + v * VEC);
+    }
+
+    __device__ __forceinline__ void smem_read(const Vec* sm, const RoundDesc& rd, uint32_t x)
+    {
+        uint32_t rv[NREG];
+        load_reg_vectors(rd, rv);
+        uint32_t pr[NREG];
+#pragma unroll
+        for (int j = 0; j < NREG; ++j) pr[j] = swz(rv[j] >> VB);
+        const uint32_t pt = swz(thread_local_index<LOG_T>(rd, x) >> VB);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) vec_to_regs<K>(sm[pt ^ reg_local_index<NREG>(pr, v)], r + v * VEC);
+    }
+};
+
+}  // namespace bitonic

@@ -1,0 +1,61 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol
+include/bitonic.h declares, and rejects bad arguments before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1506_01446_gb300 as bt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+pytestmark = pytest.mark.skipif(not os.path.exists(bt.LIB_PATH), reason="CUDA library not built")
+
+
+def header_symbols():
+    src = open(os.path.join(ROOT, "include", "bitonic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bitonic_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    lib = bt.load()
+    syms = header_symbols()
+    assert len(syms) >= 14
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) <= set(bt.EXPORTS) | set(syms)
+    assert set(bt.EXPORTS) == set(syms)
+
+
+def test_status_strings():
+    assert bt.status_string(bt.OK) == "BITONIC_OK"
+    assert bt.status_string(bt.ERR_TIMEOUT) == "BITONIC_ERR_TIMEOUT"
+
+
+def test_argument_errors_need_no_gpu():
+    lib = bt.load()
+    assert lib.bitonic_sort_u32(None, 10, 1, None) == bt.ERR_INVALID
+    assert lib.bitonic_sort_u32(3, 10, 1, None) == bt.ERR_INVALID          # misaligned
+    assert lib.bitonic_sort_u32(None, 1, 1, None) == bt.OK                 # n <= 1: nothing to do
+    assert lib.bitonic_sort_u32(None, 0, 0, None) == bt.OK
+    assert lib.bitonic_sort_u32(16, (1 << 31) + 1, 1, None) == bt.ERR_UNSUPPORTED
+    assert lib.bitonic_sort_pairs_u32(16, None, 10, 1, None) == bt.ERR_INVALID
+    assert lib.bitonic_sort_segmented_u32(16, None, 4, None) == bt.ERR_INVALID
+    assert lib.bitonic_sort_segmented_u32(16, 16, -1, None) == bt.ERR_INVALID
+    assert lib.bitonic_sort_segmented_u32(16, 16, 0, None) == bt.OK
+    assert lib.bitonic_sort_segmented_pairs_u32(16, None, 16, 3, None) == bt.ERR_INVALID
+    assert lib.bitonic_sort_u32_profiled(16, 100, 1, None, None, 0, None) == bt.ERR_INVALID
+
+
+def test_options_validation():
+    saved = bt.get_options()
+    try:
+        with pytest.raises(bt.BitonicError):
+            bt.set_options(variant=7)
+        with pytest.raises(bt.BitonicError):
+            bt.set_options(tile_log2=20)
+        bt.set_options(variant=2, tile_log2=13)
+        assert bt.get_options()["variant"] == 2
+    finally:
+        bt.set_options(**saved)

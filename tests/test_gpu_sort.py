@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path through the C ABI, bit-exact against the CPU
+oracle on seeded inputs (sorting has a unique result, so no tolerance)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1506_01446_gb300 as bt  # noqa: E402
+
+
+def to_dev(a: np.ndarray, pad_front: int = 0):
+    """uint32 numpy -> int32 CUDA tensor view (same bits); optional leading
+    elements make the returned view start 4*pad_front bytes past a 16-byte
+    boundary."""
+    buf = np.zeros(a.size + pad_front, dtype=np.uint32)
+    buf[pad_front:] = a
+    t = torch.from_numpy(buf.view(np.int32)).cuda()
+    return t[pad_front:]
+
+
+def to_host(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint32)
+
+
+@pytest.fixture(autouse=True)
+def default_options():
+    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1)
+    yield
+    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1)
+    assert bt.last_device_error() == bt.OK
+
+
+def check_keys(keys, ascending=True, pad_front=0):
+    t = to_dev(keys, pad_front)
+    bt.sort_(t, ascending)
+    torch.cuda.synchronize()
+    got = to_host(t)
+    want = oracle.merge_sort(keys, ascending)
+    assert np.array_equal(got, want), f"n={keys.size} asc={ascending} front={pad_front}"
+
+
+EDGE_SIZES = [0, 1, 2, 3, 4, 5, 7, 8, 31, 33, 1000, 4095, 4096, 4097, 8191, 8192, 8193, 16383,
+              16384, 16385, 32769, 65535, 65536, 65537, 100003, (1 << 18) + 3, (1 << 20) - 1]
+
+
+@pytest.mark.parametrize("ascending", [True, False])
+def test_edge_sizes(ascending):
+    for n in EDGE_SIZES:
+        check_keys(workloads.uniform_u32(n, seed=n + 11), ascending)
+
+
+@pytest.mark.parametrize("pad_front", [1, 2, 3])
+def test_misaligned_pointers(pad_front):
+    for n in [5, 4097, 16383, 16384, 70001, 1 << 18]:
+        check_keys(workloads.uniform_u32(n, seed=n), True, pad_front)
+        check_keys(workloads.uniform_u32(n, seed=n + 1), False, pad_front)
+
+
+def test_pad_value_keys_and_all_equal():
+    for n in [3, 1000, 16385, 1 << 17]:
+        k = workloads.uniform_u32(n, seed=5)
+        k[::3] = 0xFFFFFFFF
+        k[1::5] = 0
+        check_keys(k, True)
+        check_keys(k, False)
+        check_keys(np.full(n, 0xFFFFFFFF, dtype=np.uint32), True)
+        check_keys(np.zeros(n, dtype=np.uint32), False)
+
+
+def test_n16_uniform_workload():
+    # single array of 2^16 uniform keys, ascending (the small configuration)
+    check_keys(workloads.uniform_u32(1 << 16, seed=workloads.SEEDS["n16_uniform"]), True)
+
+
+@pytest.mark.parametrize("dist", workloads.DISTRIBUTIONS)
+def test_n24_distributions(dist):
+    keys = workloads.keys_u32(dist, 1 << 24, seed=workloads.SEEDS["n24"])
+    check_keys(keys, True)
+    check_keys(keys, False)
+
+
+def test_n24_non_power_of_two():
+    keys = workloads.uniform_u32(10_000_019, seed=workloads.SEEDS["n24_npow2"])
+    check_keys(keys, True)
+    check_keys(keys, False)
+
+
+@pytest.mark.parametrize("variant,tile", [(1, 0), (2, 0), (0, 13)])
+def test_variants_agree(variant, tile):
+    bt.set_options(variant=variant, tile_log2=tile)
+    for n in [3, 4097, 65537, 1 << 19]:
+        check_keys(workloads.uniform_u32(n, seed=n), True)
+        check_keys(workloads.uniform_u32(n, seed=n), False, 1)
+
+
+def test_without_graphs_and_on_a_side_stream():
+    bt.set_options(use_graph=0)
+    check_keys(workloads.uniform_u32(300_000, seed=1), True)
+    bt.set_options(use_graph=1)
+    s = torch.cuda.Stream()
+    keys = workloads.uniform_u32(300_001, seed=2)
+    t = to_dev(keys)
+    with torch.cuda.stream(s):
+        bt.sort_(t)
+    s.synchronize()
+    assert np.array_equal(to_host(t), oracle.merge_sort(keys))
+    # replaying the cached graph on the same buffer
+    t.copy_(to_dev(keys))
+    bt.sort_(t)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(t), oracle.merge_sort(keys))
+
+
+def test_inside_user_graph_capture():
+    keys = workloads.uniform_u32(200_000, seed=9)
+    src = to_dev(keys)
+    t = torch.empty_like(src)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        t.copy_(src)
+        bt.sort_(t)  # warm-up outside capture builds plan state
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        t.copy_(src)
+        bt.sort_(t)
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(t), oracle.merge_sort(keys))
+
+
+def test_profiled_launch_sequence():
+    n = 1 << 20
+    info = bt.plan_info(n)
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(info["launches"] + 1)]
+    keys = workloads.uniform_u32(n, seed=4)
+    t = to_dev(keys)
+    kinds = bt.sort_profiled_(t, events)
+    torch.cuda.synchronize()
+    assert kinds[: info["launches"]][0] == 0
+    assert np.array_equal(to_host(t), oracle.merge_sort(keys))
+    times = [events[i].elapsed_time(events[i + 1]) for i in range(info["launches"])]
+    assert all(x >= 0 for x in times)
+
+
+@pytest.mark.parametrize("ascending", [True, False])
+def test_pairs_small(ascending):
+    for n in [2, 3, 100, 4097, 8193, 70001, 1 << 18]:
+        keys = (workloads.uniform_u32(n, seed=n) >> np.uint32(26)).astype(np.uint32)  # many ties
+        vals = workloads.uniform_u32(n, seed=n + 7)
+        tk, tv = to_dev(keys), to_dev(vals, 1)
+        bt.sort_pairs_(tk, tv, ascending)
+        torch.cuda.synchronize()
+        wk, wv = oracle.merge_sort_pairs(keys, vals, ascending)
+        assert np.array_equal(to_host(tk), wk) and np.array_equal(to_host(tv), wv), n
+
+
+def test_pairs_n26_ties_by_index():
+    # 2^26 pairs: keys uniform over [0, 2^20), values = original index
+    keys, vals = workloads.pair_keys_u32(1 << 26, seed=workloads.SEEDS["pairs_n26"])
+    tk, tv = to_dev(keys), to_dev(vals)
+    bt.sort_pairs_(tk, tv, True)
+    torch.cuda.synchronize()
+    gk, gv = to_host(tk), to_host(tv)
+    wk, wv = oracle.merge_sort_pairs(keys, vals, True)
+    assert np.array_equal(gk, wk) and np.array_equal(gv, wv)
+
+
+def segments_case(lens, seed, gap_every=0):
+    lens = np.asarray(lens, dtype=np.int64)
+    offs = np.zeros(lens.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=offs[1:])
+    offs += 3  # offsets[0] need not be 0; starts land off 16-byte boundaries
+    keys = workloads.uniform_u32(int(offs[-1]), seed)
+    return keys, offs.astype(np.int32)
+
+
+def check_segmented(keys, offs, pairs=False):
+    tk = to_dev(keys)
+    to = torch.from_numpy(offs).cuda()
+    if pairs:
+        vals = workloads.uniform_u32(keys.size, seed=77)
+        tv = to_dev(vals)
+        bt.sort_segmented_pairs_(tk, tv, to)
+        torch.cuda.synchronize()
+        wk, wv = oracle.segmented_sort_pairs(keys, vals, offs)
+        assert np.array_equal(to_host(tk), wk) and np.array_equal(to_host(tv), wv)
+    else:
+        bt.sort_segmented_(tk, to)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(tk), oracle.segmented_sort(keys, offs))
+
+
+@pytest.mark.parametrize("pairs", [False, True])
+def test_segmented_edge_cases(pairs):
+    lens = [0, 1, 2, 3, 0, 31, 32, 33, 4095, 4096, 4097, 8191, 8192, 8193, 16383, 16384, 16385,
+            40000, 0, 1, 5]
+    keys, offs = segments_case(lens, seed=12)
+    check_segmented(keys, offs, pairs)
+
+
+def test_segmented_batched_workload():
+    # 65,536 arrays, lengths log-uniform in [1, 8192]
+    keys, offs = workloads.segmented_u32(65536, seed=workloads.SEEDS["segmented"])
+    check_segmented(keys, offs)
+
+
+def test_segmented_pairs_mixed():
+    keys, offs = workloads.segmented_u32(3000, seed=5, max_len=20000)
+    check_segmented(keys, offs, pairs=True)
+
+
+@pytest.mark.parametrize("seed", [28])
+def test_n28_uniform_full(seed):
+    # 2^28 uniform keys (1 GiB), the headline size
+    keys = workloads.uniform_u32(1 << 28, seed=workloads.SEEDS["n28_uniform"])
+    t = to_dev(keys)
+    bt.sort_(t, True)
+    torch.cuda.synchronize()
+    got = to_host(t)
+    del t
+    torch.cuda.empty_cache()
+    want = oracle.merge_sort(keys, True)
+    assert np.array_equal(got, want)

@@ -1,0 +1,84 @@
+"""Host-side tests of the launch planner: every plan is executed by a numpy
+emulation of the tile kernel (tests/plan_emulator.py) and compared with the
+oracle.  No GPU: the library is only asked for descriptors.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1506_01446_gb300 as bt
+import workloads
+from plan_emulator import Stats, emulate
+
+pytestmark = pytest.mark.skipif(not __import__("os").path.exists(bt.LIB_PATH),
+                                reason="CUDA library not built")
+
+
+@pytest.fixture(autouse=True)
+def default_options():
+    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1)
+    yield
+    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1)
+
+
+SIZES = [2, 3, 17, 4095, 4096, 8193, 16384, 16385, 70001, 1 << 17]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("ascending", [True, False])
+def test_keys_plan_sorts(n, ascending):
+    keys = workloads.uniform_u32(n, seed=n)
+    for front in (0, 1, 3):
+        st = Stats()
+        got, plan, st = emulate(keys, ascending, front, st)
+        want, _ = oracle.bitonic_sort(keys, ascending)
+        assert np.array_equal(got, want), (n, front)
+        assert st.conflicted_quarter_warps == 0
+        assert st.uncoalesced_rounds == 0
+
+
+@pytest.mark.parametrize("variant,tile", [(0, 13), (2, 0), (1, 0), (0, 14)])
+def test_other_variants_and_tiles(variant, tile):
+    bt.set_options(variant=variant, tile_log2=tile)
+    for n in (1000, 40000, 1 << 16):
+        for dist in ("uniform", "distinct16", "reverse"):
+            keys = workloads.keys_u32(dist, n, seed=3)
+            got, _, _ = emulate(keys, True, 0)
+            assert np.array_equal(got, oracle.merge_sort(keys)), (variant, tile, n, dist)
+
+
+@pytest.mark.parametrize("gb", [1, 2, 3, 5, 9])
+def test_global_bits_choices(gb):
+    bt.set_options(global_bits=gb)
+    keys = workloads.uniform_u32((1 << 18) + 5, seed=gb)
+    got, plan, _ = emulate(keys, False, 2)
+    assert np.array_equal(got, oracle.merge_sort(keys, False))
+
+
+@pytest.mark.parametrize("n", [3, 1000, 8192, 8193, 50000])
+def test_composite_plan_sorts(n):
+    # 64-bit composites (key << 32 | index), the pair sort's working array
+    keys = (workloads.uniform_u32(n, seed=n) >> np.uint32(24)).astype(np.uint64)
+    comp = (keys << np.uint64(32)) | np.arange(n, dtype=np.uint64)
+    for tile in (0, 12):
+        bt.set_options(tile_log2=tile)
+        got, _, st = emulate(comp, True, 0)
+        assert np.array_equal(got, np.sort(comp))
+        assert st.conflicted_quarter_warps == 0
+
+
+def test_plan_counts_match_section_3_2():
+    # Every plan runs exactly the k(k+1)/2 steps of the network (Section 3.2).
+    for k in (10, 14, 16, 20, 24, 28, 31):
+        for variant in (0, 1, 2):
+            bt.set_options(variant=variant)
+            info = bt.plan_info(1 << k)
+            assert info["fused_steps"] + info["global_steps"] == k * (k + 1) // 2, (k, variant)
+    bt.set_options(variant=1)
+    assert bt.plan_info(1 << 20)["launches"] == 20 * 21 // 2   # Section 3.3: one kernel per step
+
+
+def test_plan_info_headline_size():
+    info = bt.plan_info(1 << 28)
+    assert info["hbm_passes"] == info["launches"]
+    assert info["hbm_passes"] <= 40
