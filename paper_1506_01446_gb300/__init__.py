@@ -191,6 +191,9 @@ def sort_profiled_(keys, events, ascending: bool = True, stream=None):
     """Like sort_ but without a graph, recording events[i] before launch i and
     events[L] after the last; returns the kernel kind of each launch."""
     n_ev = len(events)
+    for e in events:
+        if not e.cuda_event:  # torch creates the CUDA event on first record
+            e.record()
     arr = (ctypes.c_void_p * n_ev)(*[e.cuda_event for e in events])
     kinds = (ctypes.c_int * n_ev)()
     _check(load().bitonic_sort_u32_profiled(_u32_ptr(keys, "keys"), keys.numel(), int(bool(ascending)),
