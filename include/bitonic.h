@@ -133,6 +133,7 @@ typedef struct {
     int tile_log2;        /* log2 of keys per on-chip tile; 0 = automatic */
     int global_bits;      /* strides fused per global pass; 0 = automatic */
     int use_graph;        /* 1 = replay cached CUDA graphs (default), 0 = plain launches */
+    int keys_per_thread_log2; /* log2 of keys each thread holds in registers; 0 = automatic */
 } bitonic_options;
 
 /* Process-wide options (defaults: all zero except use_graph = 1). */

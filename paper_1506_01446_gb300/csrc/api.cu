@@ -42,10 +42,10 @@ struct StreamWs {
 
 struct PlanEntry {
     Plan plan;
-    TileParams* d_descs = nullptr;
+    TileParamsBig* d_descs = nullptr;  // device copies, used by launches too big to pass by value
 };
 
-using PlanKey = std::tuple<uint64_t, int, int, int, int>;
+using PlanKey = std::tuple<uint64_t, int, int, int, int, int>;
 // op, n, ascending, ptr a, ptr b, ptr c, count, stream, variant, tile, gbits
 using GraphKey = std::tuple<int, uint64_t, int, uintptr_t, uintptr_t, uintptr_t, int, uintptr_t, int, int, int>;
 
@@ -140,7 +140,7 @@ bitonic_status get_plan(DeviceState& ds, uint64_t nv, int key_bytes, PlanEntry**
 {
     uint64_t N = 2;
     while (N < nv) N <<= 1;
-    PlanKey key{N, key_bytes, g_opt.variant, g_opt.tile_log2, g_opt.global_bits};
+    PlanKey key{N, key_bytes, g_opt.variant, g_opt.tile_log2, g_opt.global_bits, g_opt.keys_per_thread_log2};
     auto it = ds.plans.find(key);
     if (it == ds.plans.end()) {
         auto pe = std::make_unique<PlanEntry>();
@@ -149,8 +149,10 @@ bitonic_status get_plan(DeviceState& ds, uint64_t nv, int key_bytes, PlanEntry**
             t_last_error = "planner could not schedule this size";
             return BITONIC_ERR_UNSUPPORTED;
         }
-        if (!pe->plan.descs.empty()) {
-            const size_t bytes = pe->plan.descs.size() * sizeof(TileParams);
+        bool need_big = false;
+        for (const Launch& L : pe->plan.launches) need_big |= (L.desc >= 0 && !L.small);
+        if (need_big) {
+            const size_t bytes = pe->plan.descs.size() * sizeof(TileParamsBig);
             BT_CK(cudaMalloc(&pe->d_descs, bytes));
             BT_CK(cudaMemcpy(pe->d_descs, pe->plan.descs.data(), bytes, cudaMemcpyHostToDevice));
         }
@@ -173,7 +175,8 @@ bitonic_status enqueue_plan(const PlanEntry& pe, void* base, uint32_t lo, uint32
         if (L.kind == KIND_STEP)
             e = launch_step(key_bytes, desc, base, lo, hi, (uint32_t)pl.N, L.hi, L.flip, s);
         else
-            e = launch_tile(pl.cfg, desc, base, lo, hi, pe.d_descs + L.desc, L.grid, s);
+            e = launch_tile(pl.cfg, desc, base, lo, hi, L.small ? &pl.small[L.desc] : nullptr,
+                            L.small ? nullptr : pe.d_descs + L.desc, L.grid, s);
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     }
     if (events) BT_CK(cudaEventRecord(events[pl.launches.size()], s));
@@ -246,7 +249,7 @@ bitonic_status sort_u32_impl(uint32_t* keys, size_t n, int ascending, cudaStream
         if (nevents < (int)pe->plan.launches.size() + 1) return BITONIC_ERR_INVALID;
         return enqueue_plan(*pe, base, front, (uint32_t)nv, desc, 4, s, events, kinds);
     }
-    GraphKey key{0, n, desc, (uintptr_t)keys, 0, 0, 0, 0, g_opt.variant, g_opt.tile_log2, g_opt.global_bits};
+    GraphKey key{0, n, desc, (uintptr_t)keys, 0, 0, 0, 0, g_opt.variant, g_opt.tile_log2 * 16 + g_opt.keys_per_thread_log2, g_opt.global_bits};
     return run_graphed(*ds, key, s, [&](cudaStream_t cs) {
         return enqueue_plan(*pe, base, front, (uint32_t)nv, desc, 4, cs, nullptr, nullptr);
     });
@@ -269,7 +272,7 @@ bitonic_status sort_pairs_impl(uint32_t* keys, uint32_t* vals, size_t n, int asc
     const uint32_t nn = (uint32_t)n;
     uint64_t* comp = w->comp;
     GraphKey key{1, n, desc, (uintptr_t)keys, (uintptr_t)vals, (uintptr_t)comp, 0, (uintptr_t)s, g_opt.variant,
-                 g_opt.tile_log2, g_opt.global_bits};
+                 g_opt.tile_log2 * 16 + g_opt.keys_per_thread_log2, g_opt.global_bits};
     return run_graphed(*ds, key, s, [&](cudaStream_t cs) -> bitonic_status {
         BT_CK(launch_pairs_pack(comp, keys, nn, desc, cs));
         bitonic_status st2 = enqueue_plan(*pe, comp, 0, nn, 0, 8, cs, nullptr, nullptr);
@@ -431,13 +434,16 @@ bitonic_status bitonic_set_options(const bitonic_options* opt)
 {
     if (!opt) return BITONIC_ERR_INVALID;
     if (opt->variant < 0 || opt->variant > 2) return BITONIC_ERR_INVALID;
-    if (opt->tile_log2 != 0 && (opt->tile_log2 < 12 || opt->tile_log2 > 14)) return BITONIC_ERR_INVALID;
+    if (opt->tile_log2 != 0 && (opt->tile_log2 < 12 || opt->tile_log2 > 15)) return BITONIC_ERR_INVALID;
+    if (opt->keys_per_thread_log2 != 0 && (opt->keys_per_thread_log2 < 2 || opt->keys_per_thread_log2 > 7))
+        return BITONIC_ERR_INVALID;
     if (opt->global_bits < 0 || opt->global_bits > 16) return BITONIC_ERR_INVALID;
     std::lock_guard<std::mutex> g(g_mu);
     g_opt.variant = opt->variant;
     g_opt.tile_log2 = opt->tile_log2;
     g_opt.global_bits = opt->global_bits;
     g_opt.use_graph = opt->use_graph ? 1 : 0;
+    g_opt.keys_per_thread_log2 = opt->keys_per_thread_log2;
     return BITONIC_OK;
 }
 
@@ -449,6 +455,7 @@ bitonic_status bitonic_get_options(bitonic_options* opt)
     opt->tile_log2 = g_opt.tile_log2;
     opt->global_bits = g_opt.global_bits;
     opt->use_graph = g_opt.use_graph;
+    opt->keys_per_thread_log2 = g_opt.keys_per_thread_log2;
     return BITONIC_OK;
 }
 
@@ -503,10 +510,10 @@ bitonic_status bitonic_debug_plan(size_t n, int key_bytes, int* info, int max_in
         int* o = info + 6 + 7 * i;
         o[0] = L.kind; o[1] = L.phase; o[2] = L.hi; o[3] = L.lo; o[4] = L.flip; o[5] = L.desc; o[6] = (int)L.grid;
     }
-    if (descs && !p.descs.empty()) std::memcpy(descs, p.descs.data(), p.descs.size() * sizeof(TileParams));
+    if (descs && !p.descs.empty()) std::memcpy(descs, p.descs.data(), p.descs.size() * sizeof(TileParamsBig));
     return BITONIC_OK;
 }
 
-size_t bitonic_debug_desc_size(void) { return sizeof(TileParams); }
+size_t bitonic_debug_desc_size(void) { return sizeof(TileParamsBig); }
 
 }  // extern "C"

@@ -5,14 +5,15 @@
 // G(L) = XOR of gvec[j] over the set bits j of L, and g0 is the CTA's base
 // (its block index scattered into the global bits that are not in the tile).
 // Local bits 0..c-1 map to global bits 0..c-1, so the tile is made of
-// aligned rows of 2^c consecutive keys.
+// aligned rows of at least 2^c consecutive keys.
 //
 // The network runs on local indices in the mirror form: the first step of a
 // phase pairs L with L ^ (2^(b+1) - 1) (b = the phase's top bit), the others
 // pair L with L ^ 2^b, and the lower index always receives the element that
-// sorts first.  A phase's first step that spans global bits outside the tile
-// is still a local mirror step: its top local bit maps to 2^(p-1) XOR the
-// global bits below p-1 that the tile leaves out.
+// sorts first.  A phase's first step whose span reaches global bits outside
+// the tile is still a local mirror step over the whole tile: its local bit is
+// the tile's top bit and maps to 2^p XOR the global bits below p that the
+// tile leaves out.
 //
 // The steps are split into rounds.  In a round each thread holds R = 2^LOG_R
 // keys in registers: register-index bits 0..VB-1 are the components of one
@@ -26,10 +27,12 @@
 namespace bitonic {
 
 constexpr int kMaxLogThreads = 10;
-constexpr int kMaxRegBits = 5;       // LOG_R - VB
-constexpr int kMaxRounds = 100;
+constexpr int kMaxRegBits = 5;        // LOG_R - VB
+constexpr int kMaxRoundsSmall = 32;   // descriptors passed by value (constant bank)
+constexpr int kMaxRoundsBig = 100;    // descriptors read from global memory
 constexpr int kMaxStepsPerRound = 36;
 constexpr int kMaxLocalBits = 16;
+constexpr int kMaxCtaRuns = 4;
 
 // Step code: register-index bit q in bits 0..3, kStepFlip set for a mirror step.
 constexpr uint8_t kStepFlip = 16;
@@ -39,17 +42,29 @@ struct RoundDesc {
     uint16_t reg_loc[kMaxRegBits];     // local vector of register bit VB + j
     uint8_t nsteps;
     uint8_t steps[kMaxStepsPerRound];
-    uint8_t pad_[3];
+    uint8_t pad_[1];
 };
 
-struct TileParams {
-    uint32_t gvec[kMaxLocalBits];  // global vector of local bit j
-    uint8_t free_bits[32];         // global bit that receives bit i of the CTA index
-    uint8_t m;                     // local bits
-    uint8_t nfree;                 // CTA index bits
-    uint8_t contiguous;            // tile is one aligned block of 2^m positions
-    uint8_t nrounds;
-    RoundDesc rounds[kMaxRounds];
+// Global-memory side of the first (load) and last (store) rounds.
+struct IoDesc {
+    uint32_t thr_glob[kMaxLogThreads];  // G(thr_loc[i])
+    uint32_t reg_glob[kMaxRegBits];     // G(reg_loc[j])
 };
+
+template <int MAXR>
+struct TileParamsT {
+    uint32_t gvec[kMaxLocalBits];     // global vector of local bit j
+    IoDesc io[2];                     // [0] load round, [1] store round
+    uint8_t run_shift[kMaxCtaRuns];   // CTA index bits go to global bits
+    uint8_t run_width[kMaxCtaRuns];   //   run_shift[r] .. run_shift[r]+run_width[r]-1
+    uint8_t m;                        // local bits
+    uint8_t nruns;
+    uint8_t contiguous;               // tile is one aligned block of 2^m positions
+    uint8_t nrounds;
+    RoundDesc rounds[MAXR];
+};
+
+using TileParams = TileParamsT<kMaxRoundsSmall>;
+using TileParamsBig = TileParamsT<kMaxRoundsBig>;
 
 }  // namespace bitonic

@@ -116,22 +116,32 @@ __device__ __forceinline__ uint32_t reg_local_index(const uint32_t (&rv)[NREG], 
     return L;
 }
 
-// Global position of a local index: XOR of gvec over its set bits.
-__device__ __forceinline__ uint32_t global_of_local(const TileParams& P, uint32_t L)
+// CTA base position: the bits of the CTA index scattered into the runs of
+// global bits that the tile does not cover.
+template <class PT>
+__device__ __forceinline__ uint32_t cta_base(const PT& P, uint32_t cta)
 {
     uint32_t g = 0;
-    const int m = P.m;
-    for (int j = 0; j < m; ++j)
-        if ((L >> j) & 1u) g ^= P.gvec[j];
+    const int nr = P.nruns;
+#pragma unroll
+    for (int r = 0; r < kMaxCtaRuns; ++r) {
+        if (r < nr) {
+            const uint32_t w = P.run_width[r];
+            g |= (cta & ((1u << w) - 1u)) << P.run_shift[r];
+            cta >>= w;
+        }
+    }
     return g;
 }
 
-__device__ __forceinline__ uint32_t cta_base(const TileParams& P, uint32_t cta)
+// Global position of this thread's part of an I/O round's layout.
+template <int LOG_T>
+__device__ __forceinline__ uint32_t io_thread_global(const IoDesc& io, uint32_t x)
 {
     uint32_t g = 0;
-    const int nf = P.nfree;
-    for (int i = 0; i < nf; ++i)
-        if ((cta >> i) & 1u) g |= 1u << P.free_bits[i];
+#pragma unroll
+    for (int i = 0; i < LOG_T; ++i)
+        if ((x >> i) & 1u) g ^= io.thr_glob[i];
     return g;
 }
 
@@ -188,18 +198,15 @@ struct Tile {
         for (int j = 0; j < NREG; ++j) rv[j] = rd.reg_loc[j];
     }
 
-    // Global load of round rd's layout.  base points at virtual position 0;
-    // positions [lo, hi) hold real keys, others are pads.
+    // Global load in the load round's layout.  base points at virtual
+    // position 0; positions [lo, hi) hold real keys, others are pads.
     __device__ __forceinline__ void load_global(const K* __restrict__ base, uint32_t lo, uint32_t hi,
-                                                const TileParams& P, const RoundDesc& rd, uint32_t g0,
-                                                uint32_t x)
+                                                const IoDesc& io, uint32_t g0, uint32_t x)
     {
-        uint32_t rv[NREG];
-        load_reg_vectors(rd, rv);
-        const uint32_t gt = g0 ^ global_of_local(P, thread_local_index<LOG_T>(rd, x));
+        const uint32_t gt = g0 ^ io_thread_global<LOG_T>(io, x);
         uint32_t gr[NREG];
 #pragma unroll
-        for (int j = 0; j < NREG; ++j) gr[j] = global_of_local(P, rv[j]);
+        for (int j = 0; j < NREG; ++j) gr[j] = io.reg_glob[j];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const uint32_t pos = gt ^ reg_local_index<NREG>(gr, v);
@@ -217,15 +224,12 @@ struct Tile {
     }
 
     __device__ __forceinline__ void store_global(K* __restrict__ base, uint32_t lo, uint32_t hi,
-                                                 const TileParams& P, const RoundDesc& rd, uint32_t g0,
-                                                 uint32_t x)
+                                                 const IoDesc& io, uint32_t g0, uint32_t x)
     {
-        uint32_t rv[NREG];
-        load_reg_vectors(rd, rv);
-        const uint32_t gt = g0 ^ global_of_local(P, thread_local_index<LOG_T>(rd, x));
+        const uint32_t gt = g0 ^ io_thread_global<LOG_T>(io, x);
         uint32_t gr[NREG];
 #pragma unroll
-        for (int j = 0; j < NREG; ++j) gr[j] = global_of_local(P, rv[j]);
+        for (int j = 0; j < NREG; ++j) gr[j] = io.reg_glob[j];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const uint32_t pos = gt ^ reg_local_index<NREG>(gr, v);

@@ -31,6 +31,7 @@ struct Launch {
     int flip;    // 1 if the launch starts with phase p's mirror step (hi == p - 1)
     int desc;    // index into Plan::descs (-1 for KIND_STEP)
     uint32_t grid;
+    bool small;  // descriptor fits in TileParams (passed by value)
 };
 
 struct Plan {
@@ -40,7 +41,8 @@ struct Plan {
     int cfg = -1;           // tile kernel configuration (kernel_cfg.h), -1 = step kernels
     int tile_log2 = 0;
     std::vector<Launch> launches;
-    std::vector<TileParams> descs;
+    std::vector<TileParamsBig> descs;  // one per tile launch
+    std::vector<TileParams> small;     // by-value copies (valid where Launch::small)
     int hbm_passes = 0;     // launches that stream every key through HBM once
     int fused_steps = 0;    // network steps done on chip
     int global_steps = 0;   // network steps done by global passes
@@ -51,6 +53,7 @@ struct Options {
     int tile_log2 = 0;
     int global_bits = 0;
     int use_graph = 1;
+    int keys_per_thread_log2 = 0;
 };
 
 Options current_options();

@@ -3,6 +3,11 @@
 // 2^(log_r + log_t) keys in shared memory.
 #pragma once
 
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "desc.h"
+
 #define BITONIC_TILE_CONFIGS(X)                                         \
     X(0, uint32_t, 6, 8)  /* 16K keys, 256 threads x 64 keys */         \
     X(1, uint32_t, 5, 8)  /*  8K keys, 256 threads x 32 keys */         \
@@ -10,7 +15,10 @@
     X(3, uint32_t, 3, 10) /*  8K keys, 1024 threads x 8 keys (semi) */  \
     X(4, uint64_t, 5, 8)  /*  8K composites, 256 threads x 32 */        \
     X(5, uint64_t, 4, 8)  /*  4K composites, 256 threads x 16 */        \
-    X(6, uint64_t, 2, 10) /*  4K composites, 1024 threads x 4 (semi) */
+    X(6, uint64_t, 2, 10) /*  4K composites, 1024 threads x 4 (semi) */ \
+    X(7, uint32_t, 6, 9)  /* 32K keys, 512 threads x 64 keys */         \
+    X(8, uint32_t, 5, 10) /* 32K keys, 1024 threads x 32 keys */        \
+    X(9, uint64_t, 5, 9)  /* 16K composites, 512 threads x 32 */
 
 namespace bitonic {
 
@@ -21,10 +29,10 @@ struct TileCfg {
     int log_t;
 };
 
-constexpr int kNumTileCfgs = 7;
+constexpr int kNumTileCfgs = 10;
 
-cudaError_t launch_tile(int cfg, int desc, void* base, uint32_t lo, uint32_t hi, const struct TileParams* dP,
-                        uint32_t grid, cudaStream_t s);
+cudaError_t launch_tile(int cfg, int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+                        const TileParamsBig* dP, uint32_t grid, cudaStream_t s);
 cudaError_t launch_step(int key_bytes, int desc, void* base, uint32_t lo, uint32_t hi, uint32_t N, int j,
                         int flip, cudaStream_t s);
 

@@ -12,20 +12,18 @@ namespace bitonic {
 
 // One tile pass (Sections 4.1 and 4.2): load a tile of 2^m keys, run the
 // rounds (register network steps, shared-memory transposes in between), store.
-template <typename K, bool DESC, int LOG_R, int LOG_T>
-__global__ void __launch_bounds__(1 << LOG_T)
-k_tile(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParams* __restrict__ Pp)
+template <typename K, bool DESC, int LOG_R, int LOG_T, class PT>
+__device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uint32_t hi, const PT& P)
 {
     using T = Tile<K, DESC, LOG_R, LOG_T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto* sm = reinterpret_cast<typename T::Vec*>(smem_raw);
-    const TileParams& P = *Pp;
     const uint32_t x = threadIdx.x;
     const uint32_t g0 = cta_base(P, blockIdx.x);
     if (P.contiguous && g0 >= hi) return;  // the whole tile is tail padding
     T t;
     const int nr = P.nrounds;
-    t.load_global(base, lo, hi, P, P.rounds[0], g0, x);
+    t.load_global(base, lo, hi, P.io[0], g0, x);
     run_round_steps<DESC>(t.r, P.rounds[0]);
     for (int rd = 1; rd < nr; ++rd) {
         if (rd > 1) __syncthreads();
@@ -34,7 +32,23 @@ k_tile(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParams* __restr
         t.smem_read(sm, P.rounds[rd], x);
         run_round_steps<DESC>(t.r, P.rounds[rd]);
     }
-    t.store_global(base, lo, hi, P, P.rounds[nr - 1], g0, x);
+    t.store_global(base, lo, hi, P.io[1], g0, x);
+}
+
+// Descriptor passed by value: every thread reads it through the constant bank.
+template <typename K, bool DESC, int LOG_R, int LOG_T>
+__global__ void __launch_bounds__(1 << LOG_T)
+k_tile(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P)
+{
+    tile_pass<K, DESC, LOG_R, LOG_T>(base, lo, hi, P);
+}
+
+// Descriptor with more rounds than fit by value, read from global memory.
+template <typename K, bool DESC, int LOG_R, int LOG_T>
+__global__ void __launch_bounds__(1 << LOG_T)
+k_tile_big(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParamsBig* __restrict__ P)
+{
+    tile_pass<K, DESC, LOG_R, LOG_T>(base, lo, hi, *P);
 }
 
 // Section 3.3: one network step, one compare-exchange per thread.  Pair q of
@@ -90,13 +104,15 @@ __global__ void k_pairs_unpack(const uint64_t* __restrict__ comp, uint32_t* __re
 namespace {
 
 template <typename K, bool DESC, int LOG_R, int LOG_T>
-cudaError_t launch_tile_t(K* base, uint32_t lo, uint32_t hi, const TileParams* dP, uint32_t grid,
-                          cudaStream_t s)
+cudaError_t launch_tile_t(K* base, uint32_t lo, uint32_t hi, const TileParams* hP, const TileParamsBig* dP,
+                          uint32_t grid, cudaStream_t s)
 {
     constexpr int kThreads = 1 << LOG_T;
     constexpr size_t kSmem = (size_t(1) << (LOG_R + LOG_T)) * sizeof(K);
-    auto fn = k_tile<K, DESC, LOG_R, LOG_T>;
-    fn<<<grid, kThreads, kSmem, s>>>(base, lo, hi, dP);
+    if (hP)
+        k_tile<K, DESC, LOG_R, LOG_T><<<grid, kThreads, kSmem, s>>>(base, lo, hi, *hP);
+    else
+        k_tile_big<K, DESC, LOG_R, LOG_T><<<grid, kThreads, kSmem, s>>>(base, lo, hi, dP);
     return cudaGetLastError();
 }
 
@@ -112,22 +128,24 @@ cudaError_t launch_step_t(K* base, uint32_t lo, uint32_t hi, uint32_t N, int j, 
 }  // namespace
 
 template <typename KT, int LR, int LT>
-static cudaError_t launch_cfg(int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* dP,
-                              uint32_t grid, cudaStream_t s)
+static cudaError_t launch_cfg(int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+                              const TileParamsBig* dP, uint32_t grid, cudaStream_t s)
 {
     if constexpr (sizeof(KT) == 4) {
-        return desc ? launch_tile_t<KT, true, LR, LT>((KT*)base, lo, hi, dP, grid, s)
-                    : launch_tile_t<KT, false, LR, LT>((KT*)base, lo, hi, dP, grid, s);
+        return desc ? launch_tile_t<KT, true, LR, LT>((KT*)base, lo, hi, hP, dP, grid, s)
+                    : launch_tile_t<KT, false, LR, LT>((KT*)base, lo, hi, hP, dP, grid, s);
     } else {
-        return launch_tile_t<KT, false, LR, LT>((KT*)base, lo, hi, dP, grid, s);
+        return launch_tile_t<KT, false, LR, LT>((KT*)base, lo, hi, hP, dP, grid, s);
     }
 }
 
-cudaError_t launch_tile(int cfg, int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* dP,
-                        uint32_t grid, cudaStream_t s)
+// Launches one tile pass: hP (host copy, passed by value) when the
+// descriptor fits, else dP (device copy of the big descriptor).
+cudaError_t launch_tile(int cfg, int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+                        const TileParamsBig* dP, uint32_t grid, cudaStream_t s)
 {
 #define BITONIC_CFG_CASE(ID, KT, LR, LT) \
-    case ID: return launch_cfg<KT, LR, LT>(desc, base, lo, hi, dP, grid, s);
+    case ID: return launch_cfg<KT, LR, LT>(desc, base, lo, hi, hP, dP, grid, s);
     switch (cfg) {
         BITONIC_TILE_CONFIGS(BITONIC_CFG_CASE)
         default: return cudaErrorInvalidValue;
@@ -138,8 +156,11 @@ cudaError_t launch_tile(int cfg, int desc, void* base, uint32_t lo, uint32_t hi,
 template <typename K, bool DESC, int LR, int LT>
 static cudaError_t set_attr_t()
 {
-    constexpr size_t kSmem = (size_t(1) << (LR + LT)) * sizeof(K);
-    return cudaFuncSetAttribute(k_tile<K, DESC, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    constexpr int kSmem = (int)((size_t(1) << (LR + LT)) * sizeof(K));
+    cudaError_t e = cudaFuncSetAttribute(k_tile<K, DESC, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tile_big<K, DESC, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    return e;
 }
 
 template <typename KT, int LR, int LT>

@@ -1,6 +1,7 @@
 // Host planner: turns a sort of n keys into a launch sequence and builds the
 // tile descriptors (global mapping + register rounds) of every launch.
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -33,14 +34,6 @@ std::vector<LStep> tile_sort_steps(int kmax)
         s.push_back({q - 1, true});
         for (int b = q - 2; b >= 0; --b) s.push_back({b, false});
     }
-    return s;
-}
-
-// Steps at local bits top..bottom, the first one a mirror step if flip.
-std::vector<LStep> merge_steps(int top, int bottom, bool flip)
-{
-    std::vector<LStep> s;
-    for (int b = top; b >= bottom; --b) s.push_back({b, flip && b == top});
     return s;
 }
 
@@ -165,7 +158,7 @@ bool emit_round(const HostRound& hr, int log_t, int m, int vb, RoundDesc& rd)
 
 // Lanes 0..2 on local bits vb..vb+2 that the map sends to global units:
 // each quarter warp then touches one aligned 128-byte line.
-bool round_coalesced(const RoundDesc& rd, const TileParams& P, int vb)
+bool round_coalesced(const RoundDesc& rd, const TileParamsBig& P, int vb)
 {
     for (int t = 0; t < 3; ++t) {
         const int b = vb + t;
@@ -183,7 +176,22 @@ HostRound io_round(int RR, int m, int vb)
     return hr;
 }
 
-bool plan_rounds(const std::vector<LStep>& steps, const TileCfg& cfg, int vb, TileParams& P)
+uint32_t global_of_local(const TileParamsBig& P, uint32_t L)
+{
+    uint32_t g = 0;
+    for (int j = 0; j < P.m; ++j)
+        if ((L >> j) & 1u) g ^= P.gvec[j];
+    return g;
+}
+
+void fill_io(const RoundDesc& rd, const TileParamsBig& P, int log_t, int nreg, IoDesc& io)
+{
+    std::memset(&io, 0, sizeof(io));
+    for (int i = 0; i < log_t; ++i) io.thr_glob[i] = global_of_local(P, rd.thr_loc[i]);
+    for (int j = 0; j < nreg; ++j) io.reg_glob[j] = global_of_local(P, rd.reg_loc[j]);
+}
+
+bool plan_rounds(const std::vector<LStep>& steps, const TileCfg& cfg, int vb, TileParamsBig& P)
 {
     const int m = cfg.log_r + cfg.log_t;
     const int RR = cfg.log_r - vb;
@@ -196,9 +204,7 @@ bool plan_rounds(const std::vector<LStep>& steps, const TileCfg& cfg, int vb, Ti
         rounds.push_back(hr);
         i = j;
     }
-    if (rounds.empty()) {
-        rounds.push_back(io_round(RR, m, vb));
-    }
+    if (rounds.empty()) rounds.push_back(io_round(RR, m, vb));
     std::vector<RoundDesc> out;
     for (auto& hr : rounds) {
         RoundDesc rd;
@@ -211,53 +217,83 @@ bool plan_rounds(const std::vector<LStep>& steps, const TileCfg& cfg, int vb, Ti
     if (!emit_round(io_round(RR, m, vb), cfg.log_t, m, vb, io)) return false;
     if (!round_coalesced(out.front(), P, vb)) out.insert(out.begin(), io);
     if (!round_coalesced(out.back(), P, vb)) out.push_back(io);
-    if (out.size() > (size_t)kMaxRounds) return false;
+    if (out.size() > (size_t)kMaxRoundsBig) return false;
     P.nrounds = (uint8_t)out.size();
     for (size_t r = 0; r < out.size(); ++r) P.rounds[r] = out[r];
+    fill_io(out.front(), P, cfg.log_t, RR, P.io[0]);
+    fill_io(out.back(), P, cfg.log_t, RR, P.io[1]);
     return true;
 }
 
-void map_contiguous(TileParams& P, int m, int k)
+// Tile over global bits B (ascending, m of them).  With affine_top, the top
+// local bit carries a phase's mirror step: it maps to 2^top XOR every global
+// bit below top that the tile leaves out.  The CTA index fills the other
+// global bits below k, lowest first, as runs of consecutive bits.
+bool map_bits(TileParamsBig& P, const std::vector<int>& B, bool affine_top, int k)
 {
+    const int m = (int)B.size();
     P.m = (uint8_t)m;
-    for (int j = 0; j < m; ++j) P.gvec[j] = 1u << j;
-    int nf = 0;
-    for (int b = m; b < k; ++b) P.free_bits[nf++] = (uint8_t)b;
-    P.nfree = (uint8_t)nf;
-    P.contiguous = 1;
-}
-
-// Tile = rows of 2^c consecutive positions at global bits lo..hi.  With flip,
-// the top local bit carries the mirror step of phase p = hi + 1: it maps to
-// 2^hi XOR the global bits c..lo-1 that the tile leaves out.
-void map_strided(TileParams& P, int m, int c, int lo, int hi, bool flip, int k)
-{
-    P.m = (uint8_t)m;
-    for (int j = 0; j < c; ++j) P.gvec[j] = 1u << j;
-    for (int j = c; j < m; ++j) P.gvec[j] = 1u << (lo + j - c);
-    if (flip) {
-        uint32_t v = 1u << hi;
-        for (int b = c; b < lo; ++b) v |= 1u << b;
+    for (int j = 0; j < m; ++j) P.gvec[j] = 1u << B[j];
+    if (affine_top) {
+        uint32_t v = 1u << B[m - 1];
+        for (int b = 0; b < B[m - 1]; ++b)
+            if (!contains(B, b)) v |= 1u << b;
         P.gvec[m - 1] = v;
     }
-    int nf = 0;
-    for (int b = c; b < lo; ++b) P.free_bits[nf++] = (uint8_t)b;
-    for (int b = hi + 1; b < k; ++b) P.free_bits[nf++] = (uint8_t)b;
-    P.nfree = (uint8_t)nf;
-    P.contiguous = 0;
+    P.contiguous = 1;
+    for (int j = 0; j < m; ++j)
+        if (B[j] != j) P.contiguous = 0;
+    int nr = 0;
+    for (int b = 0; b < k;) {
+        if (contains(B, b)) { ++b; continue; }
+        int w = 0;
+        while (b + w < k && !contains(B, b + w)) ++w;
+        if (nr == kMaxCtaRuns) return false;
+        P.run_shift[nr] = (uint8_t)b;
+        P.run_width[nr] = (uint8_t)w;
+        ++nr;
+        b += w;
+    }
+    P.nruns = (uint8_t)nr;
+    return true;
 }
 
+// Tile configuration for a sort of key_bytes keys: the semi variant uses
+// the configurations with one register bit beyond the vector; otherwise the
+// requested tile size and keys per thread (0 = default: 16K keys of 4 bytes,
+// 8K composites of 8 bytes, 64 / 32 keys per thread).
 int choose_cfg(int key_bytes, const Options& opt)
 {
+    const int vb = key_bytes == 4 ? 2 : 1;
     const bool semi = opt.variant == 2;
-    if (key_bytes == 4) {
-        if (semi) return 3;
-        if (opt.tile_log2 == 13) return 1;
-        return 0;
+    const int tile = opt.tile_log2 ? opt.tile_log2 : (key_bytes == 4 ? 14 : 13);
+    int best = -1;
+    for (int i = 0; i < kNumTileCfgs; ++i) {
+        const TileCfg& c = kCfgs[i];
+        if (c.key_bytes != key_bytes) continue;
+        const bool c_semi = c.log_r == vb + 1;
+        if (semi != c_semi) continue;
+        if (semi) return i;
+        if (c.log_r + c.log_t != tile) continue;
+        if (opt.keys_per_thread_log2 && c.log_r != opt.keys_per_thread_log2) continue;
+        if (best < 0 || c.log_r > kCfgs[best].log_r) best = i;
     }
-    if (semi) return 6;
-    if (opt.tile_log2 == 12) return 5;
-    return 4;
+    return best;
+}
+
+struct GStep {
+    int bit;
+    bool flip;
+    int phase;
+};
+
+bool to_small(const TileParamsBig& b, TileParams& s)
+{
+    std::memset(&s, 0, sizeof(s));
+    if (b.nrounds > kMaxRoundsSmall) return false;
+    std::memcpy(&s, &b, offsetof(TileParamsBig, rounds));
+    std::memcpy(s.rounds, b.rounds, b.nrounds * sizeof(RoundDesc));
+    return true;
 }
 
 }  // namespace
@@ -274,7 +310,8 @@ Plan make_plan(uint64_t nv, int key_bytes, const Options& opt)
     plan.k = k;
     if (opt.variant == 1) {  // basic: one launch per step (Section 3.3)
         for (int p = 1; p <= k; ++p)
-            for (int j = p - 1; j >= 0; --j) plan.launches.push_back({KIND_STEP, p, j, j, j == p - 1, -1, 0});
+            for (int j = p - 1; j >= 0; --j)
+                plan.launches.push_back({KIND_STEP, p, j, j, j == p - 1, -1, 0, false});
         plan.hbm_passes = (int)plan.launches.size();
         plan.global_steps = (int)plan.launches.size();
         plan.cfg = -1;
@@ -282,61 +319,97 @@ Plan make_plan(uint64_t nv, int key_bytes, const Options& opt)
         return plan;
     }
     const int cfg_id = choose_cfg(key_bytes, opt);
+    if (cfg_id < 0) return plan;
     const TileCfg& cfg = kCfgs[cfg_id];
     const int vb = key_bytes == 4 ? 2 : 1;
     const int m = cfg.log_r + cfg.log_t;
+    const int c_min = vb + 3;  // rows of at least 128 bytes
+    const bool semi = opt.variant == 2;
+    const bool fuse = !semi;   // let a pass run across a phase boundary
+    int high_limit = semi ? 1 : (opt.global_bits > 0 ? opt.global_bits : 64);
     plan.cfg = cfg_id;
     plan.tile_log2 = m;
-    const int max_gb = m - vb - 3;
-    int gb = opt.global_bits > 0 ? opt.global_bits : max_gb;
-    if (opt.variant == 2) gb = 1;  // semi: one stride per global pass
-    gb = std::max(1, std::min(gb, max_gb));
+    const uint32_t grid = k > m ? (1u << (k - m)) : 1u;
 
-    auto add = [&](int kind, int p, int hi, int lo, bool flip, TileParams& P, uint32_t grid) {
+    auto add_pass = [&](const std::vector<int>& B, bool affine, const std::vector<LStep>& ls, int kind,
+                        int phase, int hi, int lo, bool flip) -> bool {
+        TileParamsBig P;
+        std::memset(&P, 0, sizeof(P));
+        if (!map_bits(P, B, affine, k)) return false;
+        if (!plan_rounds(ls, cfg, vb, P)) return false;
+        TileParams small;
+        const bool fits = to_small(P, small);
         plan.descs.push_back(P);
-        plan.launches.push_back({kind, p, hi, lo, flip ? 1 : 0, (int)plan.descs.size() - 1, grid});
+        plan.small.push_back(small);
+        plan.launches.push_back({kind, phase, hi, lo, flip ? 1 : 0, (int)plan.descs.size() - 1, grid, fits});
+        plan.hbm_passes += 1;
+        return true;
     };
 
+    // Phases 1..min(k, m) of every tile on chip.
     const int ksort = std::min(k, m);
     {
-        TileParams P;
-        std::memset(&P, 0, sizeof(P));
-        map_contiguous(P, m, k);
-        if (!plan_rounds(tile_sort_steps(ksort), cfg, vb, P)) return plan;
-        add(KIND_TILE_SORT, ksort, ksort - 1, 0, true, P, k > m ? (1u << (k - m)) : 1u);
+        std::vector<int> B;
+        for (int b = 0; b < m; ++b) B.push_back(b);
+        if (!add_pass(B, false, tile_sort_steps(ksort), KIND_TILE_SORT, ksort, ksort - 1, 0, true)) return plan;
         plan.fused_steps += ksort * (ksort + 1) / 2;
-        plan.hbm_passes += 1;
     }
-    int merge_desc = -1;
-    for (int p = m + 1; p <= k; ++p) {
-        const int tb = p - m;
-        const int npass = (tb + gb - 1) / gb;
-        int hi = p - 1;
-        for (int q = 0; q < npass; ++q) {
-            const int cnt = tb / npass + (q < tb % npass ? 1 : 0);
-            const int lo = hi - cnt + 1;
-            const int c = m - cnt;
-            TileParams P;
-            std::memset(&P, 0, sizeof(P));
-            map_strided(P, m, c, lo, hi, q == 0, k);
-            if (!plan_rounds(merge_steps(m - 1, c, q == 0), cfg, vb, P)) return plan;
-            add(KIND_GLOBAL, p, hi, lo, q == 0, P, 1u << (k - m));
-            plan.global_steps += cnt;
-            plan.hbm_passes += 1;
-            hi = lo - 1;
+
+    // The remaining steps, split greedily into passes: a pass takes steps
+    // while their bits (plus the 2^c_min-key rows) fit in the tile.  A
+    // phase's mirror step may open a pass or follow the previous phase's last
+    // steps, provided its bit is the highest in the tile.
+    std::vector<GStep> gs;
+    for (int p = ksort + 1; p <= k; ++p) {
+        gs.push_back({p - 1, true, p});
+        for (int b = p - 2; b >= 0; --b) gs.push_back({b, false, p});
+    }
+    size_t i = 0;
+    while (i < gs.size()) {
+        std::vector<int> B;
+        for (int b = 0; b < c_min; ++b) B.push_back(b);
+        size_t j = i;
+        int nhigh = 0;
+        bool flipped = false, has_low = false, has_high = false;
+        while (j < gs.size()) {
+            const GStep& g = gs[j];
+            const bool high = g.bit >= m;
+            if (g.flip && (flipped || B.back() > g.bit)) break;
+            if (!fuse && ((high && has_low) || (!high && has_high))) break;
+            if (high && nhigh >= high_limit) break;
+            const bool fresh = !contains(B, g.bit);
+            if (fresh && (int)B.size() == m) break;
+            if (fresh) {
+                B.push_back(g.bit);
+                std::sort(B.begin(), B.end());
+            }
+            flipped |= g.flip;
+            has_low |= !high;
+            has_high |= high;
+            nhigh += high ? 1 : 0;
+            ++j;
         }
-        if (merge_desc < 0) {
-            TileParams P;
-            std::memset(&P, 0, sizeof(P));
-            map_contiguous(P, m, k);
-            if (!plan_rounds(merge_steps(m - 1, 0, false), cfg, vb, P)) return plan;
-            add(KIND_TILE_MERGE, p, m - 1, 0, false, P, 1u << (k - m));
-            merge_desc = plan.launches.back().desc;
-        } else {
-            plan.launches.push_back({KIND_TILE_MERGE, p, m - 1, 0, 0, merge_desc, 1u << (k - m)});
+        if (j == i) return plan;
+        // Fill the tile with the lowest free bits (longer contiguous rows).
+        for (int b = 0; (int)B.size() < m; ++b)
+            if (!contains(B, b)) B.push_back(b);
+        std::sort(B.begin(), B.end());
+        std::vector<LStep> ls;
+        int hi = -1, lo = 64;
+        for (size_t s = i; s < j; ++s) {
+            const int lb = (int)(std::find(B.begin(), B.end(), gs[s].bit) - B.begin());
+            ls.push_back({lb, gs[s].flip});
+            hi = std::max(hi, gs[s].bit);
+            lo = std::min(lo, gs[s].bit);
+            if (gs[s].bit >= m) plan.global_steps += 1;
+            else plan.fused_steps += 1;
         }
-        plan.fused_steps += m;
-        plan.hbm_passes += 1;
+        bool contiguous = true;
+        for (int b = 0; b < m; ++b)
+            if (B[b] != b) contiguous = false;
+        const int kind = contiguous ? KIND_TILE_MERGE : KIND_GLOBAL;
+        if (!add_pass(B, flipped, ls, kind, gs[i].phase, hi, lo, flipped)) return plan;
+        i = j;
     }
     plan.ok = true;
     return plan;

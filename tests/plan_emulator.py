@@ -17,9 +17,11 @@ import numpy as np
 import paper_1506_01446_gb300 as bt
 
 ROUND_DT = np.dtype([("thr_loc", "<u2", 10), ("reg_loc", "<u2", 5), ("nsteps", "u1"),
-                     ("steps", "u1", 36), ("pad", "u1", 3)])
-TILE_DT = np.dtype([("gvec", "<u4", 16), ("free_bits", "u1", 32), ("m", "u1"), ("nfree", "u1"),
-                    ("contiguous", "u1"), ("nrounds", "u1"), ("rounds", ROUND_DT, 100)])
+                     ("steps", "u1", 36), ("pad", "u1", 1)])
+IO_DT = np.dtype([("thr_glob", "<u4", 10), ("reg_glob", "<u4", 5)])
+TILE_DT = np.dtype([("gvec", "<u4", 16), ("io", IO_DT, 2), ("run_shift", "u1", 4), ("run_width", "u1", 4),
+                    ("m", "u1"), ("nruns", "u1"), ("contiguous", "u1"), ("nrounds", "u1"),
+                    ("rounds", ROUND_DT, 100)])
 KIND_TILE_SORT, KIND_GLOBAL, KIND_TILE_MERGE, KIND_STEP = range(4)
 
 
@@ -136,8 +138,12 @@ def emulate(keys: np.ndarray, ascending: bool = True, front: int = 0, stats: Sta
         assert P["m"] == m
         ctas = np.arange(grid, dtype=np.int64)
         g0 = np.zeros(grid, dtype=np.int64)
-        for b in range(P["nfree"]):
-            g0 |= ((ctas >> b) & 1) << int(P["free_bits"][b])
+        rest = ctas.copy()
+        for r in range(int(P["nruns"])):
+            w = int(P["run_width"][r])
+            g0 |= (rest & ((1 << w) - 1)) << int(P["run_shift"][r])
+            rest >>= w
+        assert np.all(rest == 0), "CTA index does not fit the free bits"
         if P["contiguous"]:
             live = g0 < hi_real
             ctas, g0 = ctas[live], g0[live]
@@ -153,6 +159,12 @@ def emulate(keys: np.ndarray, ascending: bool = True, front: int = 0, stats: Sta
                        for t in range(3)):
                 stats.uncoalesced_rounds += 1
         G = _global_of_local(P["gvec"], m, np.arange(1 << m, dtype=np.int64))
+        # the precomputed I/O vectors must agree with G on their rounds
+        for io, rd in ((P["io"][0], rounds[0]), (P["io"][1], rounds[nr - 1])):
+            for t in range(log_t):
+                assert int(io["thr_glob"][t]) == int(G[int(rd["thr_loc"][t])])
+            for j in range(log_r - vb):
+                assert int(io["reg_glob"][j]) == int(G[int(rd["reg_loc"][j])])
         pos = g0[:, None] ^ G[None, :]                        # [cta, local]
         assert np.array_equal(np.sort(pos, axis=None), np.sort(np.unique(pos))), "tiles overlap"
         tile = a[pos]                                         # [cta, local] by local index
