@@ -21,18 +21,22 @@
  *   - Work is enqueued on `stream` (NULL = the legacy default stream) and the
  *     call returns without waiting.  Argument errors are reported before
  *     anything is enqueued; CUDA launch errors as BITONIC_ERR_CUDA.
- *   - Device-side failures (a bounded wait that ran out) are written to a
- *     device status word and reported by bitonic_last_device_error().
+ *   - Device-side failures (a bounded wait that ran out, or bad offsets under
+ *     BITONIC_DEBUG_CHECKS=1) are written to the device's status word and
+ *     reported by bitonic_last_device_error().
  *   - n <= 1 (or nseg == 0) returns BITONIC_OK without launching anything.
  *   - n > 2^31 returns BITONIC_ERR_UNSUPPORTED (indices are 32-bit).
  *   - Sizes that are not powers of two are padded virtually to
  *     N = next_pow2(n): positions >= n behave as keys that sort after every
  *     real key (0xFFFFFFFF ascending); they are never read or written.
  *   - The library owns a per-(device, stream) workspace (pair composites,
- *     work lists, the status word) that grows on demand with cudaMalloc and
- *     is freed by bitonic_release_workspace().  Calls on different streams
- *     may run concurrently from different host threads; calls on one stream
- *     are serialised by the caller.
+ *     work counters) that grows on demand with cudaMalloc and is freed by
+ *     bitonic_release_workspace().  Keys-only sorts need none.  Calls on
+ *     different streams may run concurrently from different host threads;
+ *     calls on one stream are serialised by the caller.  While a stream is
+ *     being captured nothing is allocated: a pair or segmented call then needs
+ *     a workspace from an earlier uncaptured call (on that stream or on the
+ *     NULL stream) and returns BITONIC_ERR_UNSUPPORTED otherwise.
  *   - When `stream` is being captured into a CUDA graph, kernels are launched
  *     straight into the capture; otherwise the library replays a cached CUDA
  *     graph of the launch sequence (keyed by size, direction, kind and
@@ -108,9 +112,10 @@ const char *bitonic_status_string(bitonic_status s);
 const char *bitonic_last_error_message(void);
 
 /*
- * Synchronises `stream`, reads and clears its device status word, and
- * returns BITONIC_OK, BITONIC_ERR_TIMEOUT or BITONIC_ERR_INVALID (debug
- * offset checks).  A stream that never ran a sort returns BITONIC_OK.
+ * Synchronises `stream`, then reads and clears the current device's status
+ * word (one per device, shared by every stream), and returns BITONIC_OK,
+ * BITONIC_ERR_TIMEOUT or BITONIC_ERR_INVALID (debug offset checks).  Work on
+ * other streams that has not finished may still set the word later.
  */
 bitonic_status bitonic_last_device_error(bitonic_stream_t stream);
 
@@ -134,6 +139,8 @@ typedef struct {
     int global_bits;      /* strides fused per global pass; 0 = automatic */
     int use_graph;        /* 1 = replay cached CUDA graphs (default), 0 = plain launches */
     int keys_per_thread_log2; /* log2 of keys each thread holds in registers; 0 = automatic */
+    int pipeline;         /* 1 = persistent CTAs that prefetch the next tile with TMA bulk copies
+                             , 0 = one CTA per tile (default) */
 } bitonic_options;
 
 /* Process-wide options (defaults: all zero except use_graph = 1). */

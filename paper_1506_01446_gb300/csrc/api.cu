@@ -58,6 +58,8 @@ struct DeviceState {
     bool inited = false;
     cudaStream_t capture = nullptr;
     int num_sms = 0;
+    int pipe_blocks[kNumTileCfgs] = {};  // resident pipelined CTAs per SM, per configuration
+    int* status = nullptr;               // device status word shared by every stream
     std::map<cudaStream_t, StreamWs> ws;
     std::map<PlanKey, std::unique_ptr<PlanEntry>> plans;
     std::map<GraphKey, GraphEntry> graphs;
@@ -96,16 +98,41 @@ bitonic_status device_state(DeviceState** out)
     if (!ds.inited) {
         BT_CK(cudaDeviceGetAttribute(&ds.num_sms, cudaDevAttrMultiProcessorCount, dev));
         BT_CK(init_tile_attributes());
+        BT_CK(init_pipe_attributes(ds.pipe_blocks));
         BT_CK(seg_init_attributes());
         BT_CK(cudaStreamCreateWithFlags(&ds.capture, cudaStreamNonBlocking));
+        BT_CK(cudaMalloc(&ds.status, sizeof(int)));
+        BT_CK(cudaMemset(ds.status, 0, sizeof(int)));
         ds.inited = true;
     }
     *out = &ds;
     return BITONIC_OK;
 }
 
+bool stream_capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cst) != cudaSuccess) return false;
+    return cst != cudaStreamCaptureStatusNone;
+}
+
+// Workspace of stream s, grown to hold comp_need composites.  While s is
+// being captured nothing can be allocated: the call then uses the stream's
+// existing workspace, or else the device's default (NULL-stream) workspace,
+// and fails if neither is large enough.
 bitonic_status stream_ws(DeviceState& ds, cudaStream_t s, size_t comp_need, StreamWs** out)
 {
+    if (stream_capturing(s)) {
+        for (cudaStream_t key : {s, (cudaStream_t) nullptr}) {
+            auto it = ds.ws.find(key);
+            if (it != ds.ws.end() && it->second.dev && it->second.comp_cap >= comp_need) {
+                *out = &it->second;
+                return BITONIC_OK;
+            }
+        }
+        t_last_error = "no workspace large enough for a captured call: run the same call once outside capture";
+        return BITONIC_ERR_UNSUPPORTED;
+    }
     StreamWs& w = ds.ws[s];
     if (!w.dev) {
         BT_CK(cudaMalloc(&w.dev, 8 * sizeof(int)));
@@ -163,8 +190,8 @@ bitonic_status get_plan(DeviceState& ds, uint64_t nv, int key_bytes, PlanEntry**
 }
 
 // Enqueues the plan's launches on `s`.  events / kinds are optional.
-bitonic_status enqueue_plan(const PlanEntry& pe, void* base, uint32_t lo, uint32_t hi, int desc,
-                            int key_bytes, cudaStream_t s, cudaEvent_t* events, int* kinds)
+bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* base, uint32_t lo, uint32_t hi,
+                            int desc, int key_bytes, int* status, cudaStream_t s, cudaEvent_t* events, int* kinds)
 {
     const Plan& pl = pe.plan;
     for (size_t i = 0; i < pl.launches.size(); ++i) {
@@ -172,11 +199,26 @@ bitonic_status enqueue_plan(const PlanEntry& pe, void* base, uint32_t lo, uint32
         if (events) BT_CK(cudaEventRecord(events[i], s));
         if (kinds) kinds[i] = L.kind;
         cudaError_t e;
-        if (L.kind == KIND_STEP)
+        if (L.kind == KIND_STEP) {
             e = launch_step(key_bytes, desc, base, lo, hi, (uint32_t)pl.N, L.hi, L.flip, s);
-        else
-            e = launch_tile(pl.cfg, desc, base, lo, hi, L.small ? &pl.small[L.desc] : nullptr,
-                            L.small ? nullptr : pe.d_descs + L.desc, L.grid, s);
+        } else {
+            const TileParams* hP = L.small ? &pl.small[L.desc] : nullptr;
+            const TileParamsBig* dP = L.small ? nullptr : pe.d_descs + L.desc;
+            const TileParamsBig& D = pl.descs[L.desc];
+            uint32_t ntiles = L.grid;
+            if (D.contiguous) {  // tiles wholly past the last key have nothing to do
+                const uint64_t live = ((uint64_t)hi + (1u << D.m) - 1) >> D.m;
+                if (live < ntiles) ntiles = (uint32_t)live;
+            }
+            const int per_sm = ds.pipe_blocks[pl.cfg];
+            if (g_opt.pipeline && per_sm > 0 && status) {
+                uint64_t g = (uint64_t)per_sm * ds.num_sms;
+                const uint32_t grid = (uint32_t)(g < ntiles ? g : ntiles);
+                e = launch_pipe(pl.cfg, desc, base, lo, hi, hP, dP, ntiles, grid, status, s);
+            } else {
+                e = launch_tile(pl.cfg, desc, base, lo, hi, hP, dP, ntiles, s);
+            }
+        }
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     }
     if (events) BT_CK(cudaEventRecord(events[pl.launches.size()], s));
@@ -245,13 +287,15 @@ bitonic_status sort_u32_impl(uint32_t* keys, size_t n, int ascending, cudaStream
     if ((st = get_plan(*ds, nv, 4, &pe))) return st;
     uint32_t* base = keys - front;
     const int desc = ascending ? 0 : 1;
+    int* status = ds->status;
     if (events) {
         if (nevents < (int)pe->plan.launches.size() + 1) return BITONIC_ERR_INVALID;
-        return enqueue_plan(*pe, base, front, (uint32_t)nv, desc, 4, s, events, kinds);
+        return enqueue_plan(*ds, *pe, base, front, (uint32_t)nv, desc, 4, status, s, events, kinds);
     }
-    GraphKey key{0, n, desc, (uintptr_t)keys, 0, 0, 0, 0, g_opt.variant, g_opt.tile_log2 * 16 + g_opt.keys_per_thread_log2, g_opt.global_bits};
+    GraphKey key{0, n, desc, (uintptr_t)keys, 0, 0, 0, 0, g_opt.variant,
+                 g_opt.tile_log2 * 16 + g_opt.keys_per_thread_log2, g_opt.global_bits * 2 + g_opt.pipeline};
     return run_graphed(*ds, key, s, [&](cudaStream_t cs) {
-        return enqueue_plan(*pe, base, front, (uint32_t)nv, desc, 4, cs, nullptr, nullptr);
+        return enqueue_plan(*ds, *pe, base, front, (uint32_t)nv, desc, 4, status, cs, nullptr, nullptr);
     });
 }
 
@@ -272,10 +316,10 @@ bitonic_status sort_pairs_impl(uint32_t* keys, uint32_t* vals, size_t n, int asc
     const uint32_t nn = (uint32_t)n;
     uint64_t* comp = w->comp;
     GraphKey key{1, n, desc, (uintptr_t)keys, (uintptr_t)vals, (uintptr_t)comp, 0, (uintptr_t)s, g_opt.variant,
-                 g_opt.tile_log2 * 16 + g_opt.keys_per_thread_log2, g_opt.global_bits};
+                 g_opt.tile_log2 * 16 + g_opt.keys_per_thread_log2, g_opt.global_bits * 2 + g_opt.pipeline};
     return run_graphed(*ds, key, s, [&](cudaStream_t cs) -> bitonic_status {
         BT_CK(launch_pairs_pack(comp, keys, nn, desc, cs));
-        bitonic_status st2 = enqueue_plan(*pe, comp, 0, nn, 0, 8, cs, nullptr, nullptr);
+        bitonic_status st2 = enqueue_plan(*ds, *pe, comp, 0, nn, 0, 8, ds->status, cs, nullptr, nullptr);
         if (st2) return st2;
         BT_CK(launch_pairs_gather(comp, vals, nn, cs));
         BT_CK(launch_pairs_unpack(comp, keys, vals, nn, desc, cs));
@@ -309,7 +353,7 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
     const int grid = seg_grid(*ds, nseg);
     if (!vals) {
         int* counter = w->dev + 1;
-        int* status = w->dev;
+        int* status = ds->status;
         GraphKey key{2, 0, 1, (uintptr_t)keys, 0, (uintptr_t)offsets, nseg, (uintptr_t)s, 0, 0, 0};
         return run_graphed(*ds, key, s, [&](cudaStream_t cs) -> bitonic_status {
             BT_CK(seg_launch_keys(keys, offsets, nseg, counter, status, debug_checks(), grid, cs));
@@ -330,7 +374,7 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
     size_t need = 0;
     if ((uint32_t)longest > kSegSmemPairs && last > first) need = (size_t)(last - first);
     if ((st = stream_ws(*ds, s, need, &w))) return st;
-    BT_CK(seg_launch_pairs(keys, vals, offsets, nseg, w->comp, first, w->dev + 1, w->dev, debug_checks(), grid, s));
+    BT_CK(seg_launch_pairs(keys, vals, offsets, nseg, w->comp, first, w->dev + 1, ds->status, debug_checks(), grid, s));
     return BITONIC_OK;
 }
 
@@ -395,12 +439,10 @@ bitonic_status bitonic_last_device_error(bitonic_stream_t stream)
     int dev = 0;
     BT_CK(cudaGetDevice(&dev));
     auto dit = g_dev.find(dev);
-    if (dit == g_dev.end()) return BITONIC_OK;
-    auto it = dit->second.ws.find(s);
-    if (it == dit->second.ws.end() || !it->second.dev) return BITONIC_OK;
+    if (dit == g_dev.end() || !dit->second.status) return BITONIC_OK;
     int word = 0;
-    BT_CK(cudaMemcpy(&word, it->second.dev, sizeof(int), cudaMemcpyDeviceToHost));
-    BT_CK(cudaMemset(it->second.dev, 0, sizeof(int)));
+    BT_CK(cudaMemcpy(&word, dit->second.status, sizeof(int), cudaMemcpyDeviceToHost));
+    BT_CK(cudaMemset(dit->second.status, 0, sizeof(int)));
     if (word == kDevOk) return BITONIC_OK;
     if (word == kDevBadOffsets) return BITONIC_ERR_INVALID;
     if (word == kDevTimeout) return BITONIC_ERR_TIMEOUT;
@@ -444,6 +486,7 @@ bitonic_status bitonic_set_options(const bitonic_options* opt)
     g_opt.global_bits = opt->global_bits;
     g_opt.use_graph = opt->use_graph ? 1 : 0;
     g_opt.keys_per_thread_log2 = opt->keys_per_thread_log2;
+    g_opt.pipeline = opt->pipeline ? 1 : 0;
     return BITONIC_OK;
 }
 
@@ -456,6 +499,7 @@ bitonic_status bitonic_get_options(bitonic_options* opt)
     opt->global_bits = g_opt.global_bits;
     opt->use_graph = g_opt.use_graph;
     opt->keys_per_thread_log2 = g_opt.keys_per_thread_log2;
+    opt->pipeline = g_opt.pipeline;
     return BITONIC_OK;
 }
 

@@ -61,6 +61,9 @@ struct TileParamsT {
     uint8_t nruns;
     uint8_t contiguous;               // tile is one aligned block of 2^m positions
     uint8_t nrounds;
+    uint8_t row_log;                  // tile rows: 2^row_log consecutive positions (local bits below
+                                      // row_log map to the same global bits)
+    uint8_t pad_[3];
     RoundDesc rounds[MAXR];
 };
 

@@ -259,6 +259,19 @@ struct Tile {
         for (int v = 0; v < NV; ++v) sm[pt ^ reg_local_index<NREG>(pr, v)] = regs_to_vec<K>(r + v * VEC);
     }
 
+    // Read of a tile stored linearly by local index (as the bulk copies land).
+    __device__ __forceinline__ void smem_read_linear(const Vec* sm, const RoundDesc& rd, uint32_t x)
+    {
+        uint32_t rv[NREG];
+        load_reg_vectors(rd, rv);
+        uint32_t pr[NREG];
+#pragma unroll
+        for (int j = 0; j < NREG; ++j) pr[j] = rv[j] >> VB;
+        const uint32_t pt = thread_local_index<LOG_T>(rd, x) >> VB;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) vec_to_regs<K>(sm[pt ^ reg_local_index<NREG>(pr, v)], r + v * VEC);
+    }
+
     __device__ __forceinline__ void smem_read(const Vec* sm, const RoundDesc& rd, uint32_t x)
     {
         uint32_t rv[NREG];

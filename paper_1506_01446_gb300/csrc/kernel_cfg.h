@@ -18,7 +18,9 @@
     X(6, uint64_t, 2, 10) /*  4K composites, 1024 threads x 4 (semi) */ \
     X(7, uint32_t, 6, 9)  /* 32K keys, 512 threads x 64 keys */         \
     X(8, uint32_t, 5, 10) /* 32K keys, 1024 threads x 32 keys */        \
-    X(9, uint64_t, 5, 9)  /* 16K composites, 512 threads x 32 */
+    X(9, uint64_t, 5, 9)  /* 16K composites, 512 threads x 32 */      \
+    X(10, uint32_t, 7, 7) /* 16K keys, 128 threads x 128 keys */       \
+    X(11, uint64_t, 6, 7) /*  8K composites, 128 threads x 64 */
 
 namespace bitonic {
 
@@ -29,10 +31,13 @@ struct TileCfg {
     int log_t;
 };
 
-constexpr int kNumTileCfgs = 10;
+constexpr int kNumTileCfgs = 12;
 
 cudaError_t launch_tile(int cfg, int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
                         const TileParamsBig* dP, uint32_t grid, cudaStream_t s);
+cudaError_t launch_pipe(int cfg, int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+                        const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, int* status, cudaStream_t s);
+cudaError_t init_pipe_attributes(int* blocks_per_sm);
 cudaError_t launch_step(int key_bytes, int desc, void* base, uint32_t lo, uint32_t hi, uint32_t N, int j,
                         int flip, cudaStream_t s);
 

@@ -1,0 +1,224 @@
+// Persistent, software-pipelined tile pass.  Each CTA walks its share of the
+// tiles; while it runs the register network on tile i (Section 4.2) and the
+// shared-memory transposes between rounds (Section 4.1), the rows of tile
+// i + grid are already in flight: TMA bulk copies (cp.async.bulk) land them
+// in a second shared-memory buffer and complete on an mbarrier.  Results go
+// from registers straight to global memory in the store round's coalesced
+// layout.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "engine.cuh"
+#include "kernel_cfg.h"
+#include "tma.cuh"
+
+namespace bitonic {
+
+namespace {
+
+// Shared memory: [landing tile][transpose tile][mbarrier][fill count][fill rows].
+template <typename K, int M>
+struct PipeSmem {
+    static constexpr size_t kTileBytes = (size_t(1) << M) * sizeof(K);
+    static constexpr int kMaxRows = 1 << (M - (sizeof(K) == 4 ? 5 : 4));
+    static constexpr size_t kBarOff = 2 * kTileBytes;
+    static constexpr size_t kCountOff = kBarOff + 8;
+    static constexpr size_t kRowsOff = kCountOff + 8;
+    static constexpr size_t kBytes = kRowsOff + 2 * kMaxRows;
+};
+
+constexpr size_t kMaxSmemPerCta = 232448;  // 227 KB opt-in limit per CTA
+
+template <class PT>
+__device__ __forceinline__ uint32_t row_global(const PT& P, int c, uint32_t r)
+{
+    uint32_t g = 0;
+    const int nb = P.m - c;
+    for (int j = 0; j < nb; ++j)
+        if ((r >> j) & 1u) g ^= P.gvec[c + j];
+    return g;
+}
+
+template <typename K, bool DESC, int LOG_R, int LOG_T, class PT>
+__device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uint32_t hi, const PT& P,
+                                          uint32_t ntiles, int* status)
+{
+    using T = Tile<K, DESC, LOG_R, LOG_T>;
+    using Vec = typename T::Vec;
+    using SM = PipeSmem<K, LOG_R + LOG_T>;
+    constexpr uint32_t kThreads = 1u << LOG_T;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    K* X = reinterpret_cast<K*>(smem_raw);
+    Vec* Y = reinterpret_cast<Vec*>(smem_raw + SM::kTileBytes);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + SM::kBarOff);
+    uint32_t* fill_count = reinterpret_cast<uint32_t*>(smem_raw + SM::kCountOff);
+    uint16_t* fill_rows = reinterpret_cast<uint16_t*>(smem_raw + SM::kRowsOff);
+
+    const uint32_t x = threadIdx.x;
+    const int c = P.row_log;
+    const uint32_t row_len = 1u << c;
+    const uint32_t nrows = 1u << (P.m - c);
+    constexpr K kFront = T::kFrontPad, kTail = T::kTailPad;
+
+    uint32_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    if (x == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+        *fill_count = 0;
+    }
+    __syncthreads();
+
+    // Rows of `t` that lie wholly in [lo, hi) go by TMA; the others are
+    // listed for the CTA to fill (with pads where outside) after the next
+    // barrier.  Ends with thread 0's arrival on the barrier.
+    auto issue = [&](uint32_t t) {
+        const uint32_t g0 = cta_base(P, t);
+        fence_proxy_async_smem();
+        for (uint32_t r = x; r < nrows; r += kThreads) {
+            const uint32_t g = g0 ^ row_global(P, c, r);
+            if (g >= lo && g + row_len <= hi) {
+                const uint32_t bytes = row_len * (uint32_t)sizeof(K);
+                asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                             : "memory");
+                tma_load_bulk(X + (size_t)r * row_len, base + g, bytes, bar);
+            } else {
+                fill_rows[atomicAdd(fill_count, 1u)] = (uint16_t)r;
+            }
+        }
+        __syncthreads();
+        if (x == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+        const uint32_t nfill = *fill_count;
+        for (uint32_t i = x; i < nfill * row_len; i += kThreads) {
+            const uint32_t r = fill_rows[i >> c];
+            const uint32_t g = (g0 ^ row_global(P, c, r)) + (i & (row_len - 1));
+            X[(size_t)r * row_len + (i & (row_len - 1))] = g < lo ? kFront : (g >= hi ? kTail : base[g]);
+        }
+    };
+
+    issue(tile);
+    uint32_t parity = 0;
+    T t;
+    for (; tile < ntiles; tile += gridDim.x) {
+        const bool ok = mbar_wait_bounded(bar, parity);
+        parity ^= 1u;
+        __syncthreads();  // fill writes of this tile are complete
+        t.smem_read_linear(reinterpret_cast<const Vec*>(X), P.rounds[0], x);
+        if (__syncthreads_or(!ok)) {
+            if (x == 0) atomicCAS(status, 0, kStatusTimeout);
+            mbar_wait_bounded(bar, parity ^ 1u);  // give copies in flight one more bounded wait
+            return;
+        }
+        const uint32_t g0 = cta_base(P, tile);
+        const uint32_t next = tile + gridDim.x;
+        if (x == 0) *fill_count = 0;
+        __syncthreads();
+        if (next < ntiles) issue(next);
+        run_round_steps<DESC>(t.r, P.rounds[0]);
+        const int nr = P.nrounds;
+        for (int rd = 1; rd < nr; ++rd) {
+            if (rd > 1) __syncthreads();
+            t.smem_write(Y, P.rounds[rd - 1], x);
+            __syncthreads();
+            t.smem_read(Y, P.rounds[rd], x);
+            run_round_steps<DESC>(t.r, P.rounds[rd]);
+        }
+        t.store_global(base, lo, hi, P.io[1], g0, x);
+        __syncthreads();
+    }
+}
+
+template <typename K, bool DESC, int LOG_R, int LOG_T>
+__global__ void __launch_bounds__(1 << LOG_T)
+k_pipe(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P, uint32_t ntiles,
+       int* status)
+{
+    pipe_pass<K, DESC, LOG_R, LOG_T>(base, lo, hi, P, ntiles, status);
+}
+
+template <typename K, bool DESC, int LOG_R, int LOG_T>
+__global__ void __launch_bounds__(1 << LOG_T)
+k_pipe_big(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParamsBig* __restrict__ P, uint32_t ntiles,
+           int* status)
+{
+    pipe_pass<K, DESC, LOG_R, LOG_T>(base, lo, hi, *P, ntiles, status);
+}
+
+template <typename K, bool DESC, int LR, int LT>
+cudaError_t launch_pipe_t(K* base, uint32_t lo, uint32_t hi, const TileParams* hP, const TileParamsBig* dP,
+                          uint32_t ntiles, uint32_t grid, int* status, cudaStream_t s)
+{
+    constexpr size_t kSmem = PipeSmem<K, LR + LT>::kBytes;
+    if constexpr (kSmem > kMaxSmemPerCta) return cudaErrorInvalidConfiguration;
+    if (hP)
+        k_pipe<K, DESC, LR, LT><<<grid, 1 << LT, kSmem, s>>>(base, lo, hi, *hP, ntiles, status);
+    else
+        k_pipe_big<K, DESC, LR, LT><<<grid, 1 << LT, kSmem, s>>>(base, lo, hi, dP, ntiles, status);
+    return cudaGetLastError();
+}
+
+template <typename K, bool DESC, int LR, int LT>
+cudaError_t pipe_attr_t(int* blocks_per_sm)
+{
+    constexpr int kSmem = (int)PipeSmem<K, LR + LT>::kBytes;
+    if constexpr (PipeSmem<K, LR + LT>::kBytes > kMaxSmemPerCta) {
+        if (blocks_per_sm) *blocks_per_sm = 0;  // two tiles do not fit: not pipelined
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_pipe<K, DESC, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pipe_big<K, DESC, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e == cudaSuccess && blocks_per_sm)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pipe<K, DESC, LR, LT>, 1 << LT, kSmem);
+    return e;
+}
+
+template <typename KT, int LR, int LT>
+cudaError_t pipe_cfg(int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* hP, const TileParamsBig* dP,
+                     uint32_t ntiles, uint32_t grid, int* status, cudaStream_t s)
+{
+    if constexpr (sizeof(KT) == 4) {
+        return desc ? launch_pipe_t<KT, true, LR, LT>((KT*)base, lo, hi, hP, dP, ntiles, grid, status, s)
+                    : launch_pipe_t<KT, false, LR, LT>((KT*)base, lo, hi, hP, dP, ntiles, grid, status, s);
+    } else {
+        return launch_pipe_t<KT, false, LR, LT>((KT*)base, lo, hi, hP, dP, ntiles, grid, status, s);
+    }
+}
+
+template <typename KT, int LR, int LT>
+cudaError_t pipe_attr_cfg(int* blocks_per_sm)
+{
+    cudaError_t e = pipe_attr_t<KT, false, LR, LT>(blocks_per_sm);
+    if constexpr (sizeof(KT) == 4) {
+        if (e == cudaSuccess) e = pipe_attr_t<KT, true, LR, LT>(nullptr);
+    }
+    return e;
+}
+
+}  // namespace
+
+cudaError_t launch_pipe(int cfg, int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+                        const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, int* status, cudaStream_t s)
+{
+#define BITONIC_PIPE_CASE(ID, KT, LR, LT) \
+    case ID: return pipe_cfg<KT, LR, LT>(desc, base, lo, hi, hP, dP, ntiles, grid, status, s);
+    switch (cfg) {
+        BITONIC_TILE_CONFIGS(BITONIC_PIPE_CASE)
+        default: return cudaErrorInvalidValue;
+    }
+#undef BITONIC_PIPE_CASE
+}
+
+// Sets the shared-memory limit of every pipelined kernel on the current
+// device and reports each configuration's resident CTAs per SM.
+cudaError_t init_pipe_attributes(int* blocks_per_sm)
+{
+    cudaError_t e = cudaSuccess;
+#define BITONIC_PIPE_ATTR(ID, KT, LR, LT) \
+    if (e == cudaSuccess) e = pipe_attr_cfg<KT, LR, LT>(&blocks_per_sm[ID]);
+    BITONIC_TILE_CONFIGS(BITONIC_PIPE_ATTR)
+#undef BITONIC_PIPE_ATTR
+    return e;
+}
+
+}  // namespace bitonic

@@ -243,6 +243,9 @@ bool map_bits(TileParamsBig& P, const std::vector<int>& B, bool affine_top, int 
     P.contiguous = 1;
     for (int j = 0; j < m; ++j)
         if (B[j] != j) P.contiguous = 0;
+    int c = 0;
+    while (c < m && P.gvec[c] == (1u << c)) ++c;
+    P.row_log = (uint8_t)c;
     int nr = 0;
     for (int b = 0; b < k;) {
         if (contains(B, b)) { ++b; continue; }

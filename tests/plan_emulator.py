@@ -21,7 +21,7 @@ ROUND_DT = np.dtype([("thr_loc", "<u2", 10), ("reg_loc", "<u2", 5), ("nsteps", "
 IO_DT = np.dtype([("thr_glob", "<u4", 10), ("reg_glob", "<u4", 5)])
 TILE_DT = np.dtype([("gvec", "<u4", 16), ("io", IO_DT, 2), ("run_shift", "u1", 4), ("run_width", "u1", 4),
                     ("m", "u1"), ("nruns", "u1"), ("contiguous", "u1"), ("nrounds", "u1"),
-                    ("rounds", ROUND_DT, 100)])
+                    ("row_log", "u1"), ("pad2", "u1", 3), ("rounds", ROUND_DT, 100)])
 KIND_TILE_SORT, KIND_GLOBAL, KIND_TILE_MERGE, KIND_STEP = range(4)
 
 
@@ -159,6 +159,9 @@ def emulate(keys: np.ndarray, ascending: bool = True, front: int = 0, stats: Sta
                        for t in range(3)):
                 stats.uncoalesced_rounds += 1
         G = _global_of_local(P["gvec"], m, np.arange(1 << m, dtype=np.int64))
+        c = int(P["row_log"])
+        assert c >= vb + 3 and all(int(P["gvec"][j]) == 1 << j for j in range(c))
+        assert c == m or int(P["gvec"][c]) != 1 << c
         # the precomputed I/O vectors must agree with G on their rounds
         for io, rd in ((P["io"][0], rounds[0]), (P["io"][1], rounds[nr - 1])):
             for t in range(log_t):

@@ -28,9 +28,9 @@ def to_host(t) -> np.ndarray:
 
 @pytest.fixture(autouse=True)
 def default_options():
-    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1)
+    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1, keys_per_thread_log2=0, pipeline=0)
     yield
-    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1)
+    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1, keys_per_thread_log2=0, pipeline=0)
     assert bt.last_device_error() == bt.OK
 
 
@@ -89,9 +89,10 @@ def test_n24_non_power_of_two():
     check_keys(keys, False)
 
 
-@pytest.mark.parametrize("variant,tile", [(1, 0), (2, 0), (0, 13)])
-def test_variants_agree(variant, tile):
-    bt.set_options(variant=variant, tile_log2=tile)
+@pytest.mark.parametrize("variant,tile,kpt,pipeline", [(1, 0, 0, 0), (2, 0, 0, 0), (0, 13, 0, 0), (0, 14, 7, 0),
+                                                      (0, 14, 6, 1), (0, 13, 5, 1), (0, 15, 6, 0)])
+def test_variants_agree(variant, tile, kpt, pipeline):
+    bt.set_options(variant=variant, tile_log2=tile, keys_per_thread_log2=kpt, pipeline=pipeline)
     for n in [3, 4097, 65537, 1 << 19]:
         check_keys(workloads.uniform_u32(n, seed=n), True)
         check_keys(workloads.uniform_u32(n, seed=n), False, 1)

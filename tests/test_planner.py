@@ -16,9 +16,9 @@ pytestmark = pytest.mark.skipif(not __import__("os").path.exists(bt.LIB_PATH),
 
 @pytest.fixture(autouse=True)
 def default_options():
-    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1)
+    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1, keys_per_thread_log2=0)
     yield
-    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1)
+    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1, keys_per_thread_log2=0)
 
 
 SIZES = [2, 3, 17, 4095, 4096, 8193, 16384, 16385, 70001, 1 << 17]
@@ -45,6 +45,20 @@ def test_other_variants_and_tiles(variant, tile):
             keys = workloads.keys_u32(dist, n, seed=3)
             got, _, _ = emulate(keys, True, 0)
             assert np.array_equal(got, oracle.merge_sort(keys)), (variant, tile, n, dist)
+
+
+@pytest.mark.parametrize("tile,kpt", [(14, 7), (14, 5), (15, 6), (15, 5), (13, 5)])
+def test_tile_configurations(tile, kpt):
+    bt.set_options(tile_log2=tile, keys_per_thread_log2=kpt)
+    for n in (3000, 1 << 17):
+        keys = workloads.uniform_u32(n, seed=kpt)
+        got, _, st = emulate(keys, True, 1)
+        assert np.array_equal(got, oracle.merge_sort(keys)), (tile, kpt, n)
+        assert st.conflicted_quarter_warps == 0
+    comp = np.arange(70001, dtype=np.uint64)[::-1].copy()
+    bt.set_options(tile_log2=0, keys_per_thread_log2=6 if kpt == 7 else 0)
+    got, _, _ = emulate(comp, True, 0)
+    assert np.array_equal(got, np.sort(comp))
 
 
 @pytest.mark.parametrize("gb", [1, 2, 3, 5, 9])
