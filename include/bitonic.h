@@ -139,6 +139,9 @@ typedef struct {
     int global_bits;      /* strides fused per global pass; 0 = automatic */
     int use_graph;        /* 1 = replay cached CUDA graphs (default), 0 = plain launches */
     int keys_per_thread_log2; /* log2 of keys each thread holds in registers; 0 = automatic */
+    int io_direct;        /* bit 0: load a tile straight into its first round's register layout,
+                             bit 1: store straight from its last round's layout (instead of an
+                             extra shared-memory transpose into a coalesced layout); 0 = off */
     int pipeline;         /* 1 = persistent CTAs that prefetch the next tile with TMA bulk copies
                              , 0 = one CTA per tile (default) */
 } bitonic_options;

@@ -41,7 +41,8 @@ class BitonicError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("tile_log2", ctypes.c_int),
                 ("global_bits", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("keys_per_thread_log2", ctypes.c_int), ("pipeline", ctypes.c_int)]
+                ("keys_per_thread_log2", ctypes.c_int), ("io_direct", ctypes.c_int),
+                ("pipeline", ctypes.c_int)]
 
 
 _lib = None
@@ -172,11 +173,11 @@ def get_options() -> dict:
 
 
 def set_options(variant=None, tile_log2=None, global_bits=None, use_graph=None,
-                keys_per_thread_log2=None, pipeline=None):
+                keys_per_thread_log2=None, io_direct=None, pipeline=None):
     cur = get_options()
     for k, v in (("variant", variant), ("tile_log2", tile_log2), ("global_bits", global_bits),
                  ("use_graph", use_graph), ("keys_per_thread_log2", keys_per_thread_log2),
-                 ("pipeline", pipeline)):
+                 ("io_direct", io_direct), ("pipeline", pipeline)):
         if v is not None:
             cur[k] = int(v)
     _check(load().bitonic_set_options(ctypes.byref(Options(**cur))), "bitonic_set_options")

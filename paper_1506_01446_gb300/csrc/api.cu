@@ -45,7 +45,7 @@ struct PlanEntry {
     TileParamsBig* d_descs = nullptr;  // device copies, used by launches too big to pass by value
 };
 
-using PlanKey = std::tuple<uint64_t, int, int, int, int, int>;
+using PlanKey = std::tuple<uint64_t, int, int, int, int, int, int>;
 // op, n, ascending, ptr a, ptr b, ptr c, count, stream, variant, tile, gbits
 using GraphKey = std::tuple<int, uint64_t, int, uintptr_t, uintptr_t, uintptr_t, int, uintptr_t, int, int, int>;
 
@@ -167,7 +167,8 @@ bitonic_status get_plan(DeviceState& ds, uint64_t nv, int key_bytes, PlanEntry**
 {
     uint64_t N = 2;
     while (N < nv) N <<= 1;
-    PlanKey key{N, key_bytes, g_opt.variant, g_opt.tile_log2, g_opt.global_bits, g_opt.keys_per_thread_log2};
+    PlanKey key{N, key_bytes, g_opt.variant, g_opt.tile_log2, g_opt.global_bits, g_opt.keys_per_thread_log2,
+                g_opt.io_direct};
     auto it = ds.plans.find(key);
     if (it == ds.plans.end()) {
         auto pe = std::make_unique<PlanEntry>();
@@ -210,13 +211,16 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
                 const uint64_t live = ((uint64_t)hi + (1u << D.m) - 1) >> D.m;
                 if (live < ntiles) ntiles = (uint32_t)live;
             }
+            // A descending sort runs ascending on ~key: complement on the
+            // first load and the last store.
+            const int cin = desc && i == 0, cout = desc && i + 1 == pl.launches.size();
             const int per_sm = ds.pipe_blocks[pl.cfg];
             if (g_opt.pipeline && per_sm > 0 && status) {
                 uint64_t g = (uint64_t)per_sm * ds.num_sms;
                 const uint32_t grid = (uint32_t)(g < ntiles ? g : ntiles);
-                e = launch_pipe(pl.cfg, desc, base, lo, hi, hP, dP, ntiles, grid, status, s);
+                e = launch_pipe(pl.cfg, base, lo, hi, hP, dP, ntiles, grid, cin, cout, status, s);
             } else {
-                e = launch_tile(pl.cfg, desc, base, lo, hi, hP, dP, ntiles, s);
+                e = launch_tile(pl.cfg, base, lo, hi, hP, dP, ntiles, cin, cout, s);
             }
         }
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -293,7 +297,7 @@ bitonic_status sort_u32_impl(uint32_t* keys, size_t n, int ascending, cudaStream
         return enqueue_plan(*ds, *pe, base, front, (uint32_t)nv, desc, 4, status, s, events, kinds);
     }
     GraphKey key{0, n, desc, (uintptr_t)keys, 0, 0, 0, 0, g_opt.variant,
-                 g_opt.tile_log2 * 16 + g_opt.keys_per_thread_log2, g_opt.global_bits * 2 + g_opt.pipeline};
+                 g_opt.tile_log2 * 16 + g_opt.keys_per_thread_log2, g_opt.global_bits * 16 + g_opt.io_direct * 2 + g_opt.pipeline};
     return run_graphed(*ds, key, s, [&](cudaStream_t cs) {
         return enqueue_plan(*ds, *pe, base, front, (uint32_t)nv, desc, 4, status, cs, nullptr, nullptr);
     });
@@ -316,7 +320,7 @@ bitonic_status sort_pairs_impl(uint32_t* keys, uint32_t* vals, size_t n, int asc
     const uint32_t nn = (uint32_t)n;
     uint64_t* comp = w->comp;
     GraphKey key{1, n, desc, (uintptr_t)keys, (uintptr_t)vals, (uintptr_t)comp, 0, (uintptr_t)s, g_opt.variant,
-                 g_opt.tile_log2 * 16 + g_opt.keys_per_thread_log2, g_opt.global_bits * 2 + g_opt.pipeline};
+                 g_opt.tile_log2 * 16 + g_opt.keys_per_thread_log2, g_opt.global_bits * 16 + g_opt.io_direct * 2 + g_opt.pipeline};
     return run_graphed(*ds, key, s, [&](cudaStream_t cs) -> bitonic_status {
         BT_CK(launch_pairs_pack(comp, keys, nn, desc, cs));
         bitonic_status st2 = enqueue_plan(*ds, *pe, comp, 0, nn, 0, 8, ds->status, cs, nullptr, nullptr);
@@ -487,6 +491,7 @@ bitonic_status bitonic_set_options(const bitonic_options* opt)
     g_opt.use_graph = opt->use_graph ? 1 : 0;
     g_opt.keys_per_thread_log2 = opt->keys_per_thread_log2;
     g_opt.pipeline = opt->pipeline ? 1 : 0;
+    g_opt.io_direct = opt->io_direct & 3;
     return BITONIC_OK;
 }
 
@@ -500,6 +505,7 @@ bitonic_status bitonic_get_options(bitonic_options* opt)
     opt->use_graph = g_opt.use_graph;
     opt->keys_per_thread_log2 = g_opt.keys_per_thread_log2;
     opt->pipeline = g_opt.pipeline;
+    opt->io_direct = g_opt.io_direct;
     return BITONIC_OK;
 }
 

@@ -42,7 +42,7 @@ struct RoundDesc {
     uint16_t reg_loc[kMaxRegBits];     // local vector of register bit VB + j
     uint8_t nsteps;
     uint8_t steps[kMaxStepsPerRound];
-    uint8_t pad_[1];
+    uint8_t pattern;                   // index into the round-pattern catalog, 0xFF = generic
 };
 
 // Global-memory side of the first (load) and last (store) rounds.
@@ -55,6 +55,8 @@ template <int MAXR>
 struct TileParamsT {
     uint32_t gvec[kMaxLocalBits];     // global vector of local bit j
     IoDesc io[2];                     // [0] load round, [1] store round
+    uint32_t span_mask;               // OR of gvec: the tile's positions lie in
+                                      // [g0 & ~span_mask, g0 | span_mask]
     uint8_t run_shift[kMaxCtaRuns];   // CTA index bits go to global bits
     uint8_t run_width[kMaxCtaRuns];   //   run_shift[r] .. run_shift[r]+run_width[r]-1
     uint8_t m;                        // local bits

@@ -201,7 +201,7 @@ struct Tile {
     // Global load in the load round's layout.  base points at virtual
     // position 0; positions [lo, hi) hold real keys, others are pads.
     __device__ __forceinline__ void load_global(const K* __restrict__ base, uint32_t lo, uint32_t hi,
-                                                const IoDesc& io, uint32_t g0, uint32_t x)
+                                                const IoDesc& io, uint32_t g0, uint32_t x, K cm)
     {
         const uint32_t gt = g0 ^ io_thread_global<LOG_T>(io, x);
         uint32_t gr[NREG];
@@ -213,18 +213,20 @@ struct Tile {
             K* dst = r + v * VEC;
             if (pos >= lo && pos + VEC <= hi) {
                 vec_to_regs<K>(*reinterpret_cast<const Vec*>(base + pos), dst);
+#pragma unroll
+                for (int c = 0; c < VEC; ++c) dst[c] ^= cm;
             } else {
 #pragma unroll
                 for (int c = 0; c < VEC; ++c) {
                     const uint32_t p = pos + c;
-                    dst[c] = p < lo ? kFrontPad : (p >= hi ? kTailPad : base[p]);
+                    dst[c] = p < lo ? kFrontPad : (p >= hi ? kTailPad : (K)(base[p] ^ cm));
                 }
             }
         }
     }
 
     __device__ __forceinline__ void store_global(K* __restrict__ base, uint32_t lo, uint32_t hi,
-                                                 const IoDesc& io, uint32_t g0, uint32_t x)
+                                                 const IoDesc& io, uint32_t g0, uint32_t x, K cm)
     {
         const uint32_t gt = g0 ^ io_thread_global<LOG_T>(io, x);
         uint32_t gr[NREG];
@@ -233,7 +235,9 @@ struct Tile {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const uint32_t pos = gt ^ reg_local_index<NREG>(gr, v);
-            const K* src = r + v * VEC;
+            K src[VEC];
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) src[c] = r[v * VEC + c] ^ cm;
             if (pos >= lo && pos + VEC <= hi) {
                 *reinterpret_cast<Vec*>(base + pos) = regs_to_vec<K>(src);
             } else if (pos + VEC > lo && pos < hi) {
@@ -259,8 +263,42 @@ struct Tile {
         for (int v = 0; v < NV; ++v) sm[pt ^ reg_local_index<NREG>(pr, v)] = regs_to_vec<K>(r + v * VEC);
     }
 
-    // Read of a tile stored linearly by local index (as the bulk copies land).
-    __device__ __forceinline__ void smem_read_linear(const Vec* sm, const RoundDesc& rd, uint32_t x)
+    // Global load / store for tiles that lie wholly inside [lo, hi).
+    __device__ __forceinline__ void load_global_interior(const K* __restrict__ base, const IoDesc& io, uint32_t g0,
+                                                         uint32_t x, K cm)
+    {
+        const uint32_t gt = g0 ^ io_thread_global<LOG_T>(io, x);
+        uint32_t gr[NREG];
+#pragma unroll
+        for (int j = 0; j < NREG; ++j) gr[j] = io.reg_glob[j];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            vec_to_regs<K>(*reinterpret_cast<const Vec*>(base + (gt ^ reg_local_index<NREG>(gr, v))), r + v * VEC);
+        if (cm) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) r[i] ^= cm;
+        }
+    }
+
+    __device__ __forceinline__ void store_global_interior(K* __restrict__ base, const IoDesc& io, uint32_t g0,
+                                                          uint32_t x, K cm)
+    {
+        if (cm) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) r[i] ^= cm;
+        }
+        const uint32_t gt = g0 ^ io_thread_global<LOG_T>(io, x);
+        uint32_t gr[NREG];
+#pragma unroll
+        for (int j = 0; j < NREG; ++j) gr[j] = io.reg_glob[j];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            *reinterpret_cast<Vec*>(base + (gt ^ reg_local_index<NREG>(gr, v))) = regs_to_vec<K>(r + v * VEC);
+    }
+
+    // Read of a tile stored linearly by local index (as the bulk copies land),
+    // complementing every key by cm.
+    __device__ __forceinline__ void smem_read_linear(const Vec* sm, const RoundDesc& rd, uint32_t x, K cm)
     {
         uint32_t rv[NREG];
         load_reg_vectors(rd, rv);
@@ -270,6 +308,10 @@ struct Tile {
         const uint32_t pt = thread_local_index<LOG_T>(rd, x) >> VB;
 #pragma unroll
         for (int v = 0; v < NV; ++v) vec_to_regs<K>(sm[pt ^ reg_local_index<NREG>(pr, v)], r + v * VEC);
+        if (cm) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) r[i] ^= cm;
+        }
     }
 
     __device__ __forceinline__ void smem_read(const Vec* sm, const RoundDesc& rd, uint32_t x)

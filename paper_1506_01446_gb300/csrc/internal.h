@@ -54,6 +54,7 @@ struct Options {
     int global_bits = 0;
     int use_graph = 1;
     int keys_per_thread_log2 = 0;
+    int io_direct = 0;
     int pipeline = 0;
 };
 

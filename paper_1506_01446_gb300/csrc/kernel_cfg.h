@@ -8,19 +8,18 @@
 
 #include "desc.h"
 
-#define BITONIC_TILE_CONFIGS(X)                                         \
+#define BITONIC_TILE_CONFIGS_U32(X)                                      \
     X(0, uint32_t, 6, 8)  /* 16K keys, 256 threads x 64 keys */         \
     X(1, uint32_t, 5, 8)  /*  8K keys, 256 threads x 32 keys */         \
     X(2, uint32_t, 5, 9)  /* 16K keys, 512 threads x 32 keys */         \
-    X(3, uint32_t, 3, 10) /*  8K keys, 1024 threads x 8 keys (semi) */  \
+    X(3, uint32_t, 3, 10) /*  8K keys, 1024 threads x 8 keys (semi) */
+
+#define BITONIC_TILE_CONFIGS_U64(X)                                      \
     X(4, uint64_t, 5, 8)  /*  8K composites, 256 threads x 32 */        \
     X(5, uint64_t, 4, 8)  /*  4K composites, 256 threads x 16 */        \
-    X(6, uint64_t, 2, 10) /*  4K composites, 1024 threads x 4 (semi) */ \
-    X(7, uint32_t, 6, 9)  /* 32K keys, 512 threads x 64 keys */         \
-    X(8, uint32_t, 5, 10) /* 32K keys, 1024 threads x 32 keys */        \
-    X(9, uint64_t, 5, 9)  /* 16K composites, 512 threads x 32 */      \
-    X(10, uint32_t, 7, 7) /* 16K keys, 128 threads x 128 keys */       \
-    X(11, uint64_t, 6, 7) /*  8K composites, 128 threads x 64 */
+    X(6, uint64_t, 2, 10) /*  4K composites, 1024 threads x 4 (semi) */
+
+#define BITONIC_TILE_CONFIGS(X) BITONIC_TILE_CONFIGS_U32(X) BITONIC_TILE_CONFIGS_U64(X)
 
 namespace bitonic {
 
@@ -31,12 +30,26 @@ struct TileCfg {
     int log_t;
 };
 
-constexpr int kNumTileCfgs = 12;
+constexpr int kNumTileCfgs = 7;
 
-cudaError_t launch_tile(int cfg, int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
-                        const TileParamsBig* dP, uint32_t grid, cudaStream_t s);
-cudaError_t launch_pipe(int cfg, int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
-                        const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, int* status, cudaStream_t s);
+const TileCfg& tile_cfg(int id);
+
+// Tile launches; complement_in / complement_out complement the keys on load /
+// store (descending 4-byte sorts run ascending on ~key).
+cudaError_t launch_tile(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+                        const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
+                        cudaStream_t s);
+cudaError_t launch_tile_u32(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+                            const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
+                            cudaStream_t s);
+cudaError_t launch_tile_u64(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+                            const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
+                            cudaStream_t s);
+cudaError_t init_tile_attributes_u32();
+cudaError_t init_tile_attributes_u64();
+cudaError_t launch_pipe(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+                        const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, int complement_in,
+                        int complement_out, int* status, cudaStream_t s);
 cudaError_t init_pipe_attributes(int* blocks_per_sm);
 cudaError_t launch_step(int key_bytes, int desc, void* base, uint32_t lo, uint32_t hi, uint32_t N, int j,
                         int flip, cudaStream_t s);

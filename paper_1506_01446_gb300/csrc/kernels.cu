@@ -1,55 +1,13 @@
-// Kernels of the single-array sort: the tile-pass kernel (tile sort, global
-// multi-stride pass and tile merge share it), the one-step kernel of the
-// basic variant, and the pack / gather / unpack kernels of the pair sort.
+// Kernels of the single-array sort besides the tile passes: the one-step
+// kernel of the basic variant and the pack / gather / unpack kernels of the
+// pair sort; plus the dispatch of tile launches to their configuration.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "engine.cuh"
 #include "internal.h"
 #include "kernel_cfg.h"
 
 namespace bitonic {
-
-// One tile pass (Sections 4.1 and 4.2): load a tile of 2^m keys, run the
-// rounds (register network steps, shared-memory transposes in between), store.
-template <typename K, bool DESC, int LOG_R, int LOG_T, class PT>
-__device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uint32_t hi, const PT& P)
-{
-    using T = Tile<K, DESC, LOG_R, LOG_T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto* sm = reinterpret_cast<typename T::Vec*>(smem_raw);
-    const uint32_t x = threadIdx.x;
-    const uint32_t g0 = cta_base(P, blockIdx.x);
-    if (P.contiguous && g0 >= hi) return;  // the whole tile is tail padding
-    T t;
-    const int nr = P.nrounds;
-    t.load_global(base, lo, hi, P.io[0], g0, x);
-    run_round_steps<DESC>(t.r, P.rounds[0]);
-    for (int rd = 1; rd < nr; ++rd) {
-        if (rd > 1) __syncthreads();
-        t.smem_write(sm, P.rounds[rd - 1], x);
-        __syncthreads();
-        t.smem_read(sm, P.rounds[rd], x);
-        run_round_steps<DESC>(t.r, P.rounds[rd]);
-    }
-    t.store_global(base, lo, hi, P.io[1], g0, x);
-}
-
-// Descriptor passed by value: every thread reads it through the constant bank.
-template <typename K, bool DESC, int LOG_R, int LOG_T>
-__global__ void __launch_bounds__(1 << LOG_T)
-k_tile(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P)
-{
-    tile_pass<K, DESC, LOG_R, LOG_T>(base, lo, hi, P);
-}
-
-// Descriptor with more rounds than fit by value, read from global memory.
-template <typename K, bool DESC, int LOG_R, int LOG_T>
-__global__ void __launch_bounds__(1 << LOG_T)
-k_tile_big(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParamsBig* __restrict__ P)
-{
-    tile_pass<K, DESC, LOG_R, LOG_T>(base, lo, hi, *P);
-}
 
 // Section 3.3: one network step, one compare-exchange per thread.  Pair q of
 // the step at stride bit j; FLIP steps pair i with i ^ (2^(j+1) - 1).
@@ -103,19 +61,6 @@ __global__ void k_pairs_unpack(const uint64_t* __restrict__ comp, uint32_t* __re
 
 namespace {
 
-template <typename K, bool DESC, int LOG_R, int LOG_T>
-cudaError_t launch_tile_t(K* base, uint32_t lo, uint32_t hi, const TileParams* hP, const TileParamsBig* dP,
-                          uint32_t grid, cudaStream_t s)
-{
-    constexpr int kThreads = 1 << LOG_T;
-    constexpr size_t kSmem = (size_t(1) << (LOG_R + LOG_T)) * sizeof(K);
-    if (hP)
-        k_tile<K, DESC, LOG_R, LOG_T><<<grid, kThreads, kSmem, s>>>(base, lo, hi, *hP);
-    else
-        k_tile_big<K, DESC, LOG_R, LOG_T><<<grid, kThreads, kSmem, s>>>(base, lo, hi, dP);
-    return cudaGetLastError();
-}
-
 template <typename K, bool DESC>
 cudaError_t launch_step_t(K* base, uint32_t lo, uint32_t hi, uint32_t N, int j, int flip, cudaStream_t s)
 {
@@ -127,61 +72,21 @@ cudaError_t launch_step_t(K* base, uint32_t lo, uint32_t hi, uint32_t N, int j, 
 
 }  // namespace
 
-template <typename KT, int LR, int LT>
-static cudaError_t launch_cfg(int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
-                              const TileParamsBig* dP, uint32_t grid, cudaStream_t s)
+cudaError_t launch_tile(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+                        const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
+                        cudaStream_t s)
 {
-    if constexpr (sizeof(KT) == 4) {
-        return desc ? launch_tile_t<KT, true, LR, LT>((KT*)base, lo, hi, hP, dP, grid, s)
-                    : launch_tile_t<KT, false, LR, LT>((KT*)base, lo, hi, hP, dP, grid, s);
-    } else {
-        return launch_tile_t<KT, false, LR, LT>((KT*)base, lo, hi, hP, dP, grid, s);
-    }
-}
-
-// Launches one tile pass: hP (host copy, passed by value) when the
-// descriptor fits, else dP (device copy of the big descriptor).
-cudaError_t launch_tile(int cfg, int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
-                        const TileParamsBig* dP, uint32_t grid, cudaStream_t s)
-{
-#define BITONIC_CFG_CASE(ID, KT, LR, LT) \
-    case ID: return launch_cfg<KT, LR, LT>(desc, base, lo, hi, hP, dP, grid, s);
-    switch (cfg) {
-        BITONIC_TILE_CONFIGS(BITONIC_CFG_CASE)
-        default: return cudaErrorInvalidValue;
-    }
-#undef BITONIC_CFG_CASE
-}
-
-template <typename K, bool DESC, int LR, int LT>
-static cudaError_t set_attr_t()
-{
-    constexpr int kSmem = (int)((size_t(1) << (LR + LT)) * sizeof(K));
-    cudaError_t e = cudaFuncSetAttribute(k_tile<K, DESC, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_tile_big<K, DESC, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    return e;
-}
-
-template <typename KT, int LR, int LT>
-static cudaError_t set_attr_cfg()
-{
-    cudaError_t e = set_attr_t<KT, false, LR, LT>();
-    if constexpr (sizeof(KT) == 4) {
-        if (e == cudaSuccess) e = set_attr_t<KT, true, LR, LT>();
-    }
-    return e;
+    if (tile_cfg(cfg).key_bytes == 4)
+        return launch_tile_u32(cfg, base, lo, hi, hP, dP, grid, complement_in, complement_out, s);
+    return launch_tile_u64(cfg, base, lo, hi, hP, dP, grid, 0, 0, s);
 }
 
 // Raises the dynamic shared-memory limit of every tile kernel on the current
 // device (must run before any launch or graph capture on that device).
 cudaError_t init_tile_attributes()
 {
-    cudaError_t e = cudaSuccess;
-#define BITONIC_CFG_ATTR(ID, KT, LR, LT) \
-    if (e == cudaSuccess) e = set_attr_cfg<KT, LR, LT>();
-    BITONIC_TILE_CONFIGS(BITONIC_CFG_ATTR)
-#undef BITONIC_CFG_ATTR
+    cudaError_t e = init_tile_attributes_u32();
+    if (e == cudaSuccess) e = init_tile_attributes_u64();
     return e;
 }
 

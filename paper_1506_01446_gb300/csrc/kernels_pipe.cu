@@ -27,8 +27,6 @@ struct PipeSmem {
     static constexpr size_t kBytes = kRowsOff + 2 * kMaxRows;
 };
 
-constexpr size_t kMaxSmemPerCta = 232448;  // 227 KB opt-in limit per CTA
-
 template <class PT>
 __device__ __forceinline__ uint32_t row_global(const PT& P, int c, uint32_t r)
 {
@@ -41,7 +39,7 @@ __device__ __forceinline__ uint32_t row_global(const PT& P, int c, uint32_t r)
 
 template <typename K, bool DESC, int LOG_R, int LOG_T, class PT>
 __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uint32_t hi, const PT& P,
-                                          uint32_t ntiles, int* status)
+                                          uint32_t ntiles, K cm_in, K cm_out, int* status)
 {
     using T = Tile<K, DESC, LOG_R, LOG_T>;
     using Vec = typename T::Vec;
@@ -92,7 +90,9 @@ __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uin
         for (uint32_t i = x; i < nfill * row_len; i += kThreads) {
             const uint32_t r = fill_rows[i >> c];
             const uint32_t g = (g0 ^ row_global(P, c, r)) + (i & (row_len - 1));
-            X[(size_t)r * row_len + (i & (row_len - 1))] = g < lo ? kFront : (g >= hi ? kTail : base[g]);
+            // pads are stored pre-complemented: the round-0 read complements every key
+            X[(size_t)r * row_len + (i & (row_len - 1))] =
+                g < lo ? (K)(kFront ^ cm_in) : (g >= hi ? (K)(kTail ^ cm_in) : base[g]);
         }
     };
 
@@ -103,7 +103,7 @@ __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uin
         const bool ok = mbar_wait_bounded(bar, parity);
         parity ^= 1u;
         __syncthreads();  // fill writes of this tile are complete
-        t.smem_read_linear(reinterpret_cast<const Vec*>(X), P.rounds[0], x);
+        t.smem_read_linear(reinterpret_cast<const Vec*>(X), P.rounds[0], x, cm_in);
         if (__syncthreads_or(!ok)) {
             if (x == 0) atomicCAS(status, 0, kStatusTimeout);
             mbar_wait_bounded(bar, parity ^ 1u);  // give copies in flight one more bounded wait
@@ -123,100 +123,86 @@ __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uin
             t.smem_read(Y, P.rounds[rd], x);
             run_round_steps<DESC>(t.r, P.rounds[rd]);
         }
-        t.store_global(base, lo, hi, P.io[1], g0, x);
+        t.store_global(base, lo, hi, P.io[1], g0, x, cm_out);
         __syncthreads();
     }
 }
 
-template <typename K, bool DESC, int LOG_R, int LOG_T>
+template <typename K, int LOG_R, int LOG_T>
 __global__ void __launch_bounds__(1 << LOG_T)
 k_pipe(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P, uint32_t ntiles,
-       int* status)
+       K cm_in, K cm_out, int* status)
 {
-    pipe_pass<K, DESC, LOG_R, LOG_T>(base, lo, hi, P, ntiles, status);
+    pipe_pass<K, false, LOG_R, LOG_T>(base, lo, hi, P, ntiles, cm_in, cm_out, status);
 }
 
-template <typename K, bool DESC, int LOG_R, int LOG_T>
+template <typename K, int LOG_R, int LOG_T>
 __global__ void __launch_bounds__(1 << LOG_T)
 k_pipe_big(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParamsBig* __restrict__ P, uint32_t ntiles,
-           int* status)
+           K cm_in, K cm_out, int* status)
 {
-    pipe_pass<K, DESC, LOG_R, LOG_T>(base, lo, hi, *P, ntiles, status);
+    pipe_pass<K, false, LOG_R, LOG_T>(base, lo, hi, *P, ntiles, cm_in, cm_out, status);
 }
 
-template <typename K, bool DESC, int LR, int LT>
-cudaError_t launch_pipe_t(K* base, uint32_t lo, uint32_t hi, const TileParams* hP, const TileParamsBig* dP,
-                          uint32_t ntiles, uint32_t grid, int* status, cudaStream_t s)
+template <typename K, int LR, int LT>
+cudaError_t launch_pipe_t(void* base, uint32_t lo, uint32_t hi, const TileParams* hP, const TileParamsBig* dP,
+                          uint32_t ntiles, uint32_t grid, int ci, int co, int* status, cudaStream_t s)
 {
     constexpr size_t kSmem = PipeSmem<K, LR + LT>::kBytes;
-    if constexpr (kSmem > kMaxSmemPerCta) return cudaErrorInvalidConfiguration;
+    const K cin = ci ? ~K(0) : K(0), cout = co ? ~K(0) : K(0);
     if (hP)
-        k_pipe<K, DESC, LR, LT><<<grid, 1 << LT, kSmem, s>>>(base, lo, hi, *hP, ntiles, status);
+        k_pipe<K, LR, LT><<<grid, 1 << LT, kSmem, s>>>((K*)base, lo, hi, *hP, ntiles, cin, cout, status);
     else
-        k_pipe_big<K, DESC, LR, LT><<<grid, 1 << LT, kSmem, s>>>(base, lo, hi, dP, ntiles, status);
+        k_pipe_big<K, LR, LT><<<grid, 1 << LT, kSmem, s>>>((K*)base, lo, hi, dP, ntiles, cin, cout, status);
     return cudaGetLastError();
 }
 
-template <typename K, bool DESC, int LR, int LT>
+template <typename K, int LR, int LT>
 cudaError_t pipe_attr_t(int* blocks_per_sm)
 {
     constexpr int kSmem = (int)PipeSmem<K, LR + LT>::kBytes;
-    if constexpr (PipeSmem<K, LR + LT>::kBytes > kMaxSmemPerCta) {
-        if (blocks_per_sm) *blocks_per_sm = 0;  // two tiles do not fit: not pipelined
-        return cudaSuccess;
-    }
-    cudaError_t e = cudaFuncSetAttribute(k_pipe<K, DESC, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_pipe<K, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pipe_big<K, DESC, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    if (e == cudaSuccess && blocks_per_sm)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pipe<K, DESC, LR, LT>, 1 << LT, kSmem);
+        e = cudaFuncSetAttribute(k_pipe_big<K, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pipe<K, LR, LT>, 1 << LT, kSmem);
     return e;
 }
 
-template <typename KT, int LR, int LT>
-cudaError_t pipe_cfg(int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* hP, const TileParamsBig* dP,
-                     uint32_t ntiles, uint32_t grid, int* status, cudaStream_t s)
-{
-    if constexpr (sizeof(KT) == 4) {
-        return desc ? launch_pipe_t<KT, true, LR, LT>((KT*)base, lo, hi, hP, dP, ntiles, grid, status, s)
-                    : launch_pipe_t<KT, false, LR, LT>((KT*)base, lo, hi, hP, dP, ntiles, grid, status, s);
-    } else {
-        return launch_pipe_t<KT, false, LR, LT>((KT*)base, lo, hi, hP, dP, ntiles, grid, status, s);
-    }
-}
-
-template <typename KT, int LR, int LT>
-cudaError_t pipe_attr_cfg(int* blocks_per_sm)
-{
-    cudaError_t e = pipe_attr_t<KT, false, LR, LT>(blocks_per_sm);
-    if constexpr (sizeof(KT) == 4) {
-        if (e == cudaSuccess) e = pipe_attr_t<KT, true, LR, LT>(nullptr);
-    }
-    return e;
-}
+// Configurations compiled in pipelined form (the others report zero CTAs
+// per SM and run one CTA per tile).
+#define BITONIC_PIPE_CONFIGS(X) \
+    X(0, uint32_t, 6, 8)        \
+    X(1, uint32_t, 5, 8)        \
+    X(4, uint64_t, 5, 8)
 
 }  // namespace
 
-cudaError_t launch_pipe(int cfg, int desc, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
-                        const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, int* status, cudaStream_t s)
+cudaError_t launch_pipe(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+                        const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, int complement_in,
+                        int complement_out, int* status, cudaStream_t s)
 {
-#define BITONIC_PIPE_CASE(ID, KT, LR, LT) \
-    case ID: return pipe_cfg<KT, LR, LT>(desc, base, lo, hi, hP, dP, ntiles, grid, status, s);
+#define BITONIC_PIPE_CASE(ID, KT, LR, LT)                                                               \
+    case ID:                                                                                            \
+        return launch_pipe_t<KT, LR, LT>(base, lo, hi, hP, dP, ntiles, grid, complement_in, complement_out, \
+                                         status, s);
     switch (cfg) {
-        BITONIC_TILE_CONFIGS(BITONIC_PIPE_CASE)
+        BITONIC_PIPE_CONFIGS(BITONIC_PIPE_CASE)
         default: return cudaErrorInvalidValue;
     }
 #undef BITONIC_PIPE_CASE
 }
 
 // Sets the shared-memory limit of every pipelined kernel on the current
-// device and reports each configuration's resident CTAs per SM.
+// device and reports each configuration's resident CTAs per SM (0 = not
+// available in pipelined form).
 cudaError_t init_pipe_attributes(int* blocks_per_sm)
 {
     cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kNumTileCfgs; ++i) blocks_per_sm[i] = 0;
 #define BITONIC_PIPE_ATTR(ID, KT, LR, LT) \
-    if (e == cudaSuccess) e = pipe_attr_cfg<KT, LR, LT>(&blocks_per_sm[ID]);
-    BITONIC_TILE_CONFIGS(BITONIC_PIPE_ATTR)
+    if (e == cudaSuccess) e = pipe_attr_t<KT, LR, LT>(&blocks_per_sm[ID]);
+    BITONIC_PIPE_CONFIGS(BITONIC_PIPE_ATTR)
 #undef BITONIC_PIPE_ATTR
     return e;
 }

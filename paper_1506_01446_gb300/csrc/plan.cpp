@@ -9,6 +9,7 @@
 #include "desc.h"
 #include "internal.h"
 #include "kernel_cfg.h"
+#include "patterns.h"
 
 namespace bitonic {
 
@@ -191,7 +192,21 @@ void fill_io(const RoundDesc& rd, const TileParamsBig& P, int log_t, int nreg, I
     for (int j = 0; j < nreg; ++j) io.reg_glob[j] = global_of_local(P, rd.reg_loc[j]);
 }
 
-bool plan_rounds(const std::vector<LStep>& steps, const TileCfg& cfg, int vb, TileParamsBig& P)
+// Index of the catalog pattern whose steps equal the round's, else generic.
+uint8_t find_pattern(const RoundDesc& rd, int log_r)
+{
+    const int n = catalog_size(log_r);
+    for (int i = 0; i < n; ++i) {
+        const RoundPattern p = catalog_pattern(log_r, i);
+        if (p.n != rd.nsteps) continue;
+        bool same = true;
+        for (int s = 0; s < p.n; ++s) same &= p.steps[s] == rd.steps[s];
+        if (same) return (uint8_t)i;
+    }
+    return kGenericPattern;
+}
+
+bool plan_rounds(const std::vector<LStep>& steps, const TileCfg& cfg, int vb, int io_direct, TileParamsBig& P)
 {
     const int m = cfg.log_r + cfg.log_t;
     const int RR = cfg.log_r - vb;
@@ -215,9 +230,10 @@ bool plan_rounds(const std::vector<LStep>& steps, const TileCfg& cfg, int vb, Ti
     // without steps (one more shared-memory transpose) where needed.
     RoundDesc io;
     if (!emit_round(io_round(RR, m, vb), cfg.log_t, m, vb, io)) return false;
-    if (!round_coalesced(out.front(), P, vb)) out.insert(out.begin(), io);
-    if (!round_coalesced(out.back(), P, vb)) out.push_back(io);
+    if (!(io_direct & 1) && !round_coalesced(out.front(), P, vb)) out.insert(out.begin(), io);
+    if (!(io_direct & 2) && !round_coalesced(out.back(), P, vb)) out.push_back(io);
     if (out.size() > (size_t)kMaxRoundsBig) return false;
+    for (RoundDesc& rd : out) rd.pattern = find_pattern(rd, cfg.log_r);
     P.nrounds = (uint8_t)out.size();
     for (size_t r = 0; r < out.size(); ++r) P.rounds[r] = out[r];
     fill_io(out.front(), P, cfg.log_t, RR, P.io[0]);
@@ -246,6 +262,8 @@ bool map_bits(TileParamsBig& P, const std::vector<int>& B, bool affine_top, int 
     int c = 0;
     while (c < m && P.gvec[c] == (1u << c)) ++c;
     P.row_log = (uint8_t)c;
+    P.span_mask = 0;
+    for (int j = 0; j < m; ++j) P.span_mask |= P.gvec[j];
     int nr = 0;
     for (int b = 0; b < k;) {
         if (contains(B, b)) { ++b; continue; }
@@ -270,6 +288,9 @@ int choose_cfg(int key_bytes, const Options& opt)
     const int vb = key_bytes == 4 ? 2 : 1;
     const bool semi = opt.variant == 2;
     const int tile = opt.tile_log2 ? opt.tile_log2 : (key_bytes == 4 ? 14 : 13);
+    // Default keys per thread: 64 for 4-byte keys, 32 for composites, else
+    // the largest configured value below that.
+    const int pref_r = opt.keys_per_thread_log2 ? opt.keys_per_thread_log2 : (key_bytes == 4 ? 6 : 5);
     int best = -1;
     for (int i = 0; i < kNumTileCfgs; ++i) {
         const TileCfg& c = kCfgs[i];
@@ -279,6 +300,7 @@ int choose_cfg(int key_bytes, const Options& opt)
         if (semi) return i;
         if (c.log_r + c.log_t != tile) continue;
         if (opt.keys_per_thread_log2 && c.log_r != opt.keys_per_thread_log2) continue;
+        if (c.log_r > pref_r) continue;
         if (best < 0 || c.log_r > kCfgs[best].log_r) best = i;
     }
     return best;
@@ -339,7 +361,7 @@ Plan make_plan(uint64_t nv, int key_bytes, const Options& opt)
         TileParamsBig P;
         std::memset(&P, 0, sizeof(P));
         if (!map_bits(P, B, affine, k)) return false;
-        if (!plan_rounds(ls, cfg, vb, P)) return false;
+        if (!plan_rounds(ls, cfg, vb, opt.io_direct, P)) return false;
         TileParams small;
         const bool fits = to_small(P, small);
         plan.descs.push_back(P);

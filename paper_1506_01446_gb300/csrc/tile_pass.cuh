@@ -1,0 +1,153 @@
+// Tile-pass kernel templates (Sections 4.1 and 4.2), instantiated per key
+// type in tile_u32.cu and tile_u64.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "engine.cuh"
+#include "patterns.h"
+
+namespace bitonic {
+
+// Steps of catalog pattern IDX, unrolled at compile time (straight-line code,
+// so the register allocator can rename freely inside a round).
+template <int LOG_R, int IDX, int S, bool DESC, typename K, int R>
+__device__ __forceinline__ void pattern_steps(K (&r)[R])
+{
+    constexpr RoundPattern p = catalog_pattern(LOG_R, IDX);
+    if constexpr (S < p.n) {
+        constexpr int code = p.steps[S];
+        net_step<code & 15, (code & kStepFlip) != 0, DESC>(r);
+        pattern_steps<LOG_R, IDX, S + 1, DESC>(r);
+    }
+}
+
+// Runs a round's steps on registers that stay in place (round 0 and the
+// last round): a catalog pattern, else the per-step dispatcher.
+template <int LOG_R, bool DESC, int I = 0, typename K, int R>
+__device__ __forceinline__ void steps_in_place(K (&r)[R], const RoundDesc& rd)
+{
+    if constexpr (I < catalog_size(LOG_R)) {
+        if (rd.pattern == I) {
+            pattern_steps<LOG_R, I, 0, DESC>(r);
+            return;
+        }
+        steps_in_place<LOG_R, DESC, I + 1>(r, rd);
+    } else {
+        run_round_steps<DESC>(r, rd);
+    }
+}
+
+// A middle round: shared-memory read, steps, shared-memory write, with the
+// registers local to the round.
+template <typename K, bool DESC, int LOG_R, int LOG_T, bool CATALOG, int I = 0>
+__device__ __forceinline__ void middle_round(typename Tile<K, DESC, LOG_R, LOG_T>::Vec* sm, const RoundDesc& rd,
+                                             uint32_t x)
+{
+    using T = Tile<K, DESC, LOG_R, LOG_T>;
+    if constexpr (CATALOG && I < catalog_size(LOG_R)) {
+        if (rd.pattern == I) {
+            T u;
+            u.smem_read(sm, rd, x);
+            pattern_steps<LOG_R, I, 0, DESC>(u.r);
+            __syncthreads();
+            u.smem_write(sm, rd, x);
+            return;
+        }
+        middle_round<K, DESC, LOG_R, LOG_T, CATALOG, I + 1>(sm, rd, x);
+    } else {
+        T u;
+        u.smem_read(sm, rd, x);
+        run_round_steps<DESC>(u.r, rd);
+        __syncthreads();
+        u.smem_write(sm, rd, x);
+    }
+}
+
+// One tile pass (Sections 4.1 and 4.2): load a tile of 2^m keys, run the
+// rounds (register network steps, shared-memory transposes in between), store.
+template <typename K, bool DESC, int LOG_R, int LOG_T, bool CATALOG, class PT>
+__device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uint32_t hi, const PT& P, K cm_in,
+                                          K cm_out)
+{
+    using T = Tile<K, DESC, LOG_R, LOG_T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto* sm = reinterpret_cast<typename T::Vec*>(smem_raw);
+    const uint32_t x = threadIdx.x;
+    const uint32_t g0 = cta_base(P, blockIdx.x);
+    if (P.contiguous && g0 >= hi) return;  // the whole tile is tail padding
+    const bool interior = (g0 & ~P.span_mask) >= lo && (g0 | P.span_mask) < hi;
+    const int nr = P.nrounds;
+    T t;
+    if (interior)
+        t.load_global_interior(base, P.io[0], g0, x, cm_in);
+    else
+        t.load_global(base, lo, hi, P.io[0], g0, x, cm_in);
+    constexpr int kCat = CATALOG ? LOG_R : 0;  // catalog_size(0) == 0: per-step dispatch only
+    steps_in_place<kCat, DESC>(t.r, P.rounds[0]);
+    if (nr > 1) {
+        t.smem_write(sm, P.rounds[0], x);
+        for (int rd = 1; rd < nr - 1; ++rd) {
+            __syncthreads();
+            middle_round<K, DESC, LOG_R, LOG_T, CATALOG>(sm, P.rounds[rd], x);
+        }
+        __syncthreads();
+        t.smem_read(sm, P.rounds[nr - 1], x);
+        steps_in_place<kCat, DESC>(t.r, P.rounds[nr - 1]);
+    }
+    if (interior)
+        t.store_global_interior(base, P.io[1], g0, x, cm_out);
+    else
+        t.store_global(base, lo, hi, P.io[1], g0, x, cm_out);
+}
+
+// Descriptor passed by value: every thread reads it through the constant
+// bank.  Keys are complemented on load / store when cm_in / cm_out are all
+// ones (a descending sort runs as an ascending sort of ~key).
+template <typename K, int LOG_R, int LOG_T>
+__global__ void __launch_bounds__(1 << LOG_T)
+k_tile(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P, K cm_in, K cm_out)
+{
+    tile_pass<K, false, LOG_R, LOG_T, true>(base, lo, hi, P, cm_in, cm_out);
+}
+
+// Descriptor with more rounds than fit by value, read from global memory.
+template <typename K, int LOG_R, int LOG_T>
+__global__ void __launch_bounds__(1 << LOG_T)
+k_tile_big(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParamsBig* __restrict__ P, K cm_in, K cm_out)
+{
+    tile_pass<K, false, LOG_R, LOG_T, false>(base, lo, hi, *P, cm_in, cm_out);
+}
+
+// Launcher and attribute setup of one configuration.
+template <typename K, int LR, int LT>
+cudaError_t launch_tile_t(void* base, uint32_t lo, uint32_t hi, const TileParams* hP, const TileParamsBig* dP,
+                          uint32_t grid, int complement_in, int complement_out, cudaStream_t s)
+{
+    constexpr int kThreads = 1 << LT;
+    constexpr size_t kSmem = (size_t(1) << (LR + LT)) * sizeof(K);
+    const K ci = complement_in ? ~K(0) : K(0), co = complement_out ? ~K(0) : K(0);
+    if (hP)
+        k_tile<K, LR, LT><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, *hP, ci, co);
+    else
+        k_tile_big<K, LR, LT><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, dP, ci, co);
+    return cudaGetLastError();
+}
+
+template <typename K, int LR, int LT>
+cudaError_t tile_attr_t()
+{
+    constexpr int kSmem = (int)((size_t(1) << (LR + LT)) * sizeof(K));
+    cudaError_t e = cudaFuncSetAttribute(k_tile<K, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tile_big<K, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    // Prefer the largest shared-memory carve-out so that every CTA the
+    // registers allow can be resident.
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tile<K, LR, LT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+}
+
+
+}  // namespace bitonic

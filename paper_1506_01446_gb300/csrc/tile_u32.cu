@@ -1,0 +1,30 @@
+// Tile-pass kernels for 4-byte keys.
+#include "kernel_cfg.h"
+#include "tile_pass.cuh"
+
+namespace bitonic {
+
+cudaError_t launch_tile_u32(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+                            const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
+                            cudaStream_t s)
+{
+#define BITONIC_CASE(ID, KT, LR, LT) \
+    case ID: return launch_tile_t<KT, LR, LT>(base, lo, hi, hP, dP, grid, complement_in, complement_out, s);
+    switch (cfg) {
+        BITONIC_TILE_CONFIGS_U32(BITONIC_CASE)
+        default: return cudaErrorInvalidValue;
+    }
+#undef BITONIC_CASE
+}
+
+cudaError_t init_tile_attributes_u32()
+{
+    cudaError_t e = cudaSuccess;
+#define BITONIC_ATTR(ID, KT, LR, LT) \
+    if (e == cudaSuccess) e = tile_attr_t<KT, LR, LT>();
+    BITONIC_TILE_CONFIGS_U32(BITONIC_ATTR)
+#undef BITONIC_ATTR
+    return e;
+}
+
+}  // namespace bitonic

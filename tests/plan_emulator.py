@@ -17,9 +17,10 @@ import numpy as np
 import paper_1506_01446_gb300 as bt
 
 ROUND_DT = np.dtype([("thr_loc", "<u2", 10), ("reg_loc", "<u2", 5), ("nsteps", "u1"),
-                     ("steps", "u1", 36), ("pad", "u1", 1)])
+                     ("steps", "u1", 36), ("pattern", "u1")])
 IO_DT = np.dtype([("thr_glob", "<u4", 10), ("reg_glob", "<u4", 5)])
-TILE_DT = np.dtype([("gvec", "<u4", 16), ("io", IO_DT, 2), ("run_shift", "u1", 4), ("run_width", "u1", 4),
+TILE_DT = np.dtype([("gvec", "<u4", 16), ("io", IO_DT, 2), ("span_mask", "<u4"), ("run_shift", "u1", 4),
+                    ("run_width", "u1", 4),
                     ("m", "u1"), ("nruns", "u1"), ("contiguous", "u1"), ("nrounds", "u1"),
                     ("row_log", "u1"), ("pad2", "u1", 3), ("rounds", ROUND_DT, 100)])
 KIND_TILE_SORT, KIND_GLOBAL, KIND_TILE_MERGE, KIND_STEP = range(4)
@@ -157,7 +158,7 @@ def emulate(keys: np.ndarray, ascending: bool = True, front: int = 0, stats: Sta
             thr = rounds[idx]["thr_loc"]
             if not all(int(thr[t]) == 1 << (vb + t) and int(P["gvec"][vb + t]) == 1 << (vb + t)
                        for t in range(3)):
-                stats.uncoalesced_rounds += 1
+                stats.uncoalesced_rounds += 1   # allowed only with io_direct
         G = _global_of_local(P["gvec"], m, np.arange(1 << m, dtype=np.int64))
         c = int(P["row_log"])
         assert c >= vb + 3 and all(int(P["gvec"][j]) == 1 << j for j in range(c))

@@ -47,7 +47,7 @@ def test_other_variants_and_tiles(variant, tile):
             assert np.array_equal(got, oracle.merge_sort(keys)), (variant, tile, n, dist)
 
 
-@pytest.mark.parametrize("tile,kpt", [(14, 7), (14, 5), (15, 6), (15, 5), (13, 5)])
+@pytest.mark.parametrize("tile,kpt", [(14, 6), (14, 5), (13, 5)])
 def test_tile_configurations(tile, kpt):
     bt.set_options(tile_log2=tile, keys_per_thread_log2=kpt)
     for n in (3000, 1 << 17):
@@ -56,9 +56,19 @@ def test_tile_configurations(tile, kpt):
         assert np.array_equal(got, oracle.merge_sort(keys)), (tile, kpt, n)
         assert st.conflicted_quarter_warps == 0
     comp = np.arange(70001, dtype=np.uint64)[::-1].copy()
-    bt.set_options(tile_log2=0, keys_per_thread_log2=6 if kpt == 7 else 0)
+    bt.set_options(tile_log2=0, keys_per_thread_log2=0)
     got, _, _ = emulate(comp, True, 0)
     assert np.array_equal(got, np.sort(comp))
+
+
+@pytest.mark.parametrize("io_direct", [1, 2, 3])
+def test_direct_io_layouts(io_direct):
+    bt.set_options(io_direct=io_direct)
+    for n in (5000, (1 << 18) + 1):
+        keys = workloads.uniform_u32(n, seed=io_direct)
+        got, _, st = emulate(keys, False, 2)
+        assert np.array_equal(got, oracle.merge_sort(keys, False))
+    bt.set_options(io_direct=0)
 
 
 @pytest.mark.parametrize("gb", [1, 2, 3, 5, 9])
