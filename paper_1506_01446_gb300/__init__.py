@@ -28,7 +28,7 @@ EXPORTS = (
     "bitonic_sort_segmented_pairs_u32", "bitonic_status_string", "bitonic_last_error_message",
     "bitonic_last_device_error", "bitonic_release_workspace", "bitonic_set_options",
     "bitonic_get_options", "bitonic_plan_info", "bitonic_sort_u32_profiled", "bitonic_debug_plan",
-    "bitonic_debug_desc_size",
+    "bitonic_debug_desc_size", "bitonic_sort_pairs_u32_noalloc",
 )
 
 
@@ -76,6 +76,7 @@ def load() -> ctypes.CDLL:
     lib.bitonic_debug_plan.argtypes = [sz, i32, pint, i32, vp, i32]
     lib.bitonic_debug_desc_size.argtypes = []
     lib.bitonic_debug_desc_size.restype = sz
+    lib.bitonic_sort_pairs_u32_noalloc.argtypes = [vp, vp, sz, i32, vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if f.restype is ctypes.c_int or f.restype is None:
