@@ -142,8 +142,9 @@ typedef struct {
     int io_direct;        /* bit 0: load a tile straight into its first round's register layout,
                              bit 1: store straight from its last round's layout (instead of an
                              extra shared-memory transpose into a coalesced layout); 0 = off */
-    int pipeline;         /* 1 = persistent CTAs that prefetch the next tile with TMA bulk copies
-                             , 0 = one CTA per tile (default) */
+    int pipeline;         /* 0 = one CTA per tile (default); persistent CTAs that prefetch the
+                             next tile into shared memory with 1 = TMA bulk copies per row,
+                             2 = per-thread 16-byte cp.async copies */
 } bitonic_options;
 
 /* Process-wide options (defaults: all zero except use_graph = 1). */

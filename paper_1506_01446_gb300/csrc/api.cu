@@ -218,7 +218,7 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
             if (g_opt.pipeline && per_sm > 0 && status) {
                 uint64_t g = (uint64_t)per_sm * ds.num_sms;
                 const uint32_t grid = (uint32_t)(g < ntiles ? g : ntiles);
-                e = launch_pipe(pl.cfg, base, lo, hi, hP, dP, ntiles, grid, cin, cout, status, s);
+                e = launch_pipe(g_opt.pipeline, pl.cfg, base, lo, hi, hP, dP, ntiles, grid, cin, cout, status, s);
             } else {
                 e = launch_tile(pl.cfg, base, lo, hi, hP, dP, ntiles, cin, cout, s);
             }
@@ -490,7 +490,7 @@ bitonic_status bitonic_set_options(const bitonic_options* opt)
     g_opt.global_bits = opt->global_bits;
     g_opt.use_graph = opt->use_graph ? 1 : 0;
     g_opt.keys_per_thread_log2 = opt->keys_per_thread_log2;
-    g_opt.pipeline = opt->pipeline ? 1 : 0;
+    g_opt.pipeline = (opt->pipeline >= 0 && opt->pipeline <= 2) ? opt->pipeline : 0;
     g_opt.io_direct = opt->io_direct & 3;
     return BITONIC_OK;
 }

@@ -47,7 +47,7 @@ cudaError_t launch_tile_u64(int cfg, void* base, uint32_t lo, uint32_t hi, const
                             cudaStream_t s);
 cudaError_t init_tile_attributes_u32();
 cudaError_t init_tile_attributes_u64();
-cudaError_t launch_pipe(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+cudaError_t launch_pipe(int mode, int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
                         const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, int complement_in,
                         int complement_out, int* status, cudaStream_t s);
 cudaError_t init_pipe_attributes(int* blocks_per_sm);

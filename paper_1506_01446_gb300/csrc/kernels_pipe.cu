@@ -37,7 +37,7 @@ __device__ __forceinline__ uint32_t row_global(const PT& P, int c, uint32_t r)
     return g;
 }
 
-template <typename K, bool DESC, int LOG_R, int LOG_T, class PT>
+template <int ASYNC, typename K, bool DESC, int LOG_R, int LOG_T, class PT>
 __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uint32_t hi, const PT& P,
                                           uint32_t ntiles, K cm_in, K cm_out, int* status)
 {
@@ -69,24 +69,23 @@ __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uin
 
     // Rows of `t` that lie wholly in [lo, hi) go by TMA; the others are
     // listed for the CTA to fill (with pads where outside) after the next
-    // barrier.  Ends with thread 0's arrival on the barrier.
-    auto issue = [&](uint32_t t) {
+    // barrier.  The copies may complete before the byte count is announced:
+    // the barrier's transaction count goes below zero until thread 0's
+    // arrive.expect_tx adds the total, and the phase cannot complete before
+    // that arrival.
+    auto issue_tma = [&](uint32_t t) {
         const uint32_t g0 = cta_base(P, t);
         fence_proxy_async_smem();
         for (uint32_t r = x; r < nrows; r += kThreads) {
             const uint32_t g = g0 ^ row_global(P, c, r);
-            if (g >= lo && g + row_len <= hi) {
-                const uint32_t bytes = row_len * (uint32_t)sizeof(K);
-                asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                             : "memory");
-                tma_load_bulk(X + (size_t)r * row_len, base + g, bytes, bar);
-            } else {
+            if (g >= lo && g + row_len <= hi)
+                tma_load_bulk(X + (size_t)r * row_len, base + g, row_len * (uint32_t)sizeof(K), bar);
+            else
                 fill_rows[atomicAdd(fill_count, 1u)] = (uint16_t)r;
-            }
         }
         __syncthreads();
-        if (x == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
         const uint32_t nfill = *fill_count;
+        if (x == 0) mbar_arrive_expect_tx(bar, (nrows - nfill) * row_len * (uint32_t)sizeof(K));
         for (uint32_t i = x; i < nfill * row_len; i += kThreads) {
             const uint32_t r = fill_rows[i >> c];
             const uint32_t g = (g0 ^ row_global(P, c, r)) + (i & (row_len - 1));
@@ -96,17 +95,58 @@ __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uin
         }
     };
 
+    // The same prefetch with per-thread 16-byte cp.async copies in the load
+    // round's coalesced layout (linear by local index in X).
+    auto issue_cpasync = [&](uint32_t t) {
+        const uint32_t g0 = cta_base(P, t);
+        const RoundDesc& rd = P.rounds[0];
+        const IoDesc& io = P.io[0];
+        const uint32_t Lt = thread_local_index<LOG_T>(rd, x);
+        const uint32_t gt = g0 ^ io_thread_global<LOG_T>(io, x);
+#pragma unroll
+        for (int v = 0; v < T::NV; ++v) {
+            uint32_t L = Lt, g = gt;
+#pragma unroll
+            for (int j = 0; j < T::NREG; ++j)
+                if ((v >> j) & 1) {
+                    L ^= rd.reg_loc[j];
+                    g ^= io.reg_glob[j];
+                }
+            K* dst = X + L;
+            if (g >= lo && g + T::VEC <= hi) {
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(base + g)
+                             : "memory");
+            } else {
+#pragma unroll
+                for (int c2 = 0; c2 < T::VEC; ++c2) {
+                    const uint32_t p = g + c2;
+                    dst[c2] = p < lo ? (K)(kFront ^ cm_in) : (p >= hi ? (K)(kTail ^ cm_in) : base[p]);
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto issue = [&](uint32_t t) {
+        if constexpr (ASYNC == 0) issue_tma(t);
+        else issue_cpasync(t);
+    };
+
     issue(tile);
     uint32_t parity = 0;
     T t;
     for (; tile < ntiles; tile += gridDim.x) {
-        const bool ok = mbar_wait_bounded(bar, parity);
-        parity ^= 1u;
+        bool ok = true;
+        if constexpr (ASYNC == 0) {
+            ok = mbar_wait_bounded(bar, parity);
+            parity ^= 1u;
+        } else {
+            asm volatile("cp.async.wait_all;" ::: "memory");
+        }
         __syncthreads();  // fill writes of this tile are complete
         t.smem_read_linear(reinterpret_cast<const Vec*>(X), P.rounds[0], x, cm_in);
         if (__syncthreads_or(!ok)) {
             if (x == 0) atomicCAS(status, 0, kStatusTimeout);
-            mbar_wait_bounded(bar, parity ^ 1u);  // give copies in flight one more bounded wait
+            if constexpr (ASYNC == 0) mbar_wait_bounded(bar, parity ^ 1u);  // one more bounded wait for copies
             return;
         }
         const uint32_t g0 = cta_base(P, tile);
@@ -128,32 +168,40 @@ __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uin
     }
 }
 
-template <typename K, int LOG_R, int LOG_T>
+template <int ASYNC, typename K, int LOG_R, int LOG_T>
 __global__ void __launch_bounds__(1 << LOG_T)
 k_pipe(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P, uint32_t ntiles,
        K cm_in, K cm_out, int* status)
 {
-    pipe_pass<K, false, LOG_R, LOG_T>(base, lo, hi, P, ntiles, cm_in, cm_out, status);
+    pipe_pass<ASYNC, K, false, LOG_R, LOG_T>(base, lo, hi, P, ntiles, cm_in, cm_out, status);
 }
 
-template <typename K, int LOG_R, int LOG_T>
+template <int ASYNC, typename K, int LOG_R, int LOG_T>
 __global__ void __launch_bounds__(1 << LOG_T)
 k_pipe_big(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParamsBig* __restrict__ P, uint32_t ntiles,
            K cm_in, K cm_out, int* status)
 {
-    pipe_pass<K, false, LOG_R, LOG_T>(base, lo, hi, *P, ntiles, cm_in, cm_out, status);
+    pipe_pass<ASYNC, K, false, LOG_R, LOG_T>(base, lo, hi, *P, ntiles, cm_in, cm_out, status);
 }
 
 template <typename K, int LR, int LT>
-cudaError_t launch_pipe_t(void* base, uint32_t lo, uint32_t hi, const TileParams* hP, const TileParamsBig* dP,
-                          uint32_t ntiles, uint32_t grid, int ci, int co, int* status, cudaStream_t s)
+cudaError_t launch_pipe_t(int mode, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+                          const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, int ci, int co, int* status,
+                          cudaStream_t s)
 {
     constexpr size_t kSmem = PipeSmem<K, LR + LT>::kBytes;
     const K cin = ci ? ~K(0) : K(0), cout = co ? ~K(0) : K(0);
-    if (hP)
-        k_pipe<K, LR, LT><<<grid, 1 << LT, kSmem, s>>>((K*)base, lo, hi, *hP, ntiles, cin, cout, status);
-    else
-        k_pipe_big<K, LR, LT><<<grid, 1 << LT, kSmem, s>>>((K*)base, lo, hi, dP, ntiles, cin, cout, status);
+    if (mode == 2) {
+        if (hP)
+            k_pipe<1, K, LR, LT><<<grid, 1 << LT, kSmem, s>>>((K*)base, lo, hi, *hP, ntiles, cin, cout, status);
+        else
+            k_pipe_big<1, K, LR, LT><<<grid, 1 << LT, kSmem, s>>>((K*)base, lo, hi, dP, ntiles, cin, cout, status);
+    } else {
+        if (hP)
+            k_pipe<0, K, LR, LT><<<grid, 1 << LT, kSmem, s>>>((K*)base, lo, hi, *hP, ntiles, cin, cout, status);
+        else
+            k_pipe_big<0, K, LR, LT><<<grid, 1 << LT, kSmem, s>>>((K*)base, lo, hi, dP, ntiles, cin, cout, status);
+    }
     return cudaGetLastError();
 }
 
@@ -161,11 +209,13 @@ template <typename K, int LR, int LT>
 cudaError_t pipe_attr_t(int* blocks_per_sm)
 {
     constexpr int kSmem = (int)PipeSmem<K, LR + LT>::kBytes;
-    cudaError_t e = cudaFuncSetAttribute(k_pipe<K, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    cudaError_t e = cudaSuccess;
+    for (auto fn : {k_pipe<0, K, LR, LT>, k_pipe<1, K, LR, LT>})
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    for (auto fn : {k_pipe_big<0, K, LR, LT>, k_pipe_big<1, K, LR, LT>})
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pipe_big<K, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pipe<K, LR, LT>, 1 << LT, kSmem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pipe<0, K, LR, LT>, 1 << LT, kSmem);
     return e;
 }
 
@@ -178,13 +228,13 @@ cudaError_t pipe_attr_t(int* blocks_per_sm)
 
 }  // namespace
 
-cudaError_t launch_pipe(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
+cudaError_t launch_pipe(int mode, int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
                         const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, int complement_in,
                         int complement_out, int* status, cudaStream_t s)
 {
-#define BITONIC_PIPE_CASE(ID, KT, LR, LT)                                                               \
-    case ID:                                                                                            \
-        return launch_pipe_t<KT, LR, LT>(base, lo, hi, hP, dP, ntiles, grid, complement_in, complement_out, \
+#define BITONIC_PIPE_CASE(ID, KT, LR, LT)                                                                   \
+    case ID:                                                                                                \
+        return launch_pipe_t<KT, LR, LT>(mode, base, lo, hi, hP, dP, ntiles, grid, complement_in, complement_out, \
                                          status, s);
     switch (cfg) {
         BITONIC_PIPE_CONFIGS(BITONIC_PIPE_CASE)

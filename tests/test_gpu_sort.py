@@ -90,7 +90,7 @@ def test_n24_non_power_of_two():
 
 
 @pytest.mark.parametrize("variant,tile,kpt,pipeline", [(1, 0, 0, 0), (2, 0, 0, 0), (0, 13, 0, 0), (0, 14, 5, 0),
-                                                      (0, 14, 6, 1), (0, 13, 5, 1)])
+                                                      (0, 14, 6, 1), (0, 13, 5, 1), (0, 14, 6, 2), (0, 13, 5, 2)])
 def test_variants_agree(variant, tile, kpt, pipeline):
     bt.set_options(variant=variant, tile_log2=tile, keys_per_thread_log2=kpt, pipeline=pipeline)
     for n in [3, 4097, 65537, 1 << 19]:
