@@ -43,7 +43,103 @@ def parse():
     ap.add_argument("--n-log2", type=int, default=28, help="keys per array = 2^n_log2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e / per-kernel legs")
+    ap.add_argument("--no-segmented", action="store_true", help="skip the batched segmented leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop leg")
+    ap.add_argument("--serving-requests", type=int, default=20000)
     return ap.parse_args()
+
+
+KERNEL_SOURCES = ("engine.cuh", "tile_pass.cuh", "tile_u32.cu", "desc.h", "patterns.h", "plan.cpp")
+
+
+def kernel_source_hash():
+    """Hash of the sources that define the tile-pass kernel and its plans."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1506_01446_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(n):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, scaled to n keys -- or None if the kernel changed since."""
+    p = os.path.join(ROOT, "profiles", "traffic_global_pass.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d["bytes_per_launch"] * n / d["n"]
+
+
+def segmented_leg(bt, torch, steps):
+    """65,536 uint32 arrays (lengths log-uniform in [1, 8192]) sorted by one
+    batched segmented call vs one bitonic_sort_u32 call per array."""
+    keys_np, offs_np = workloads.segmented_u32(65536, seed=workloads.SEEDS["segmented"])
+    src = torch.from_numpy(keys_np.view(np.int32)).cuda()
+    buf = src.clone()
+    offs = torch.from_numpy(offs_np).cuda()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        buf.copy_(src)
+        bt.sort_segmented_(buf, offs)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        buf.copy_(src)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bt.sort_segmented_(buf, offs)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    batched_ms = statistics.median(times)
+    # per-array form: one plain launch sequence per array, same stream
+    lib = bt.load()
+    saved = bt.get_options()
+    bt.set_options(use_graph=0)
+    base = buf.data_ptr()
+    lens = np.diff(offs_np).tolist()
+    ptrs = (base + 4 * offs_np[:-1].astype(np.int64)).tolist()
+    sh = stream.cuda_stream
+    for p, n in zip(ptrs[:256], lens[:256]):
+        lib.bitonic_sort_u32(p, n, 1, sh)
+    buf.copy_(src)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    f = lib.bitonic_sort_u32
+    for p, n in zip(ptrs, lens):
+        f(p, n, 1, sh)
+    b.record(stream)
+    torch.cuda.synchronize()
+    per_array_ms = a.elapsed_time(b)
+    bt.set_options(**saved)
+    out = buf.cpu().numpy().view(np.uint32)
+    ok = all(np.all(np.diff(out[offs_np[i]:offs_np[i + 1]].astype(np.int64)) >= 0) for i in range(0, 65536, 97))
+    nkeys = int(offs_np[-1] - offs_np[0])
+    return {"arrays": 65536, "keys": nkeys, "batched_ms": batched_ms, "batched_gkeys_s": nkeys / batched_ms / 1e6,
+            "per_array_ms": per_array_ms, "speedup": per_array_ms / batched_ms, "sampled_sorted": bool(ok),
+            "note": "per-array form = 65,536 bitonic_sort_u32 calls (plain launches) on one stream"}
+
+
+def serving_leg(bt, requests):
+    """Poisson stream at 2,000 req/s, sizes log-uniform in [2^10, 2^22] keys,
+    30% with values, 16 GiB device budget, continuous batching."""
+    from paper_1506_01446_gb300.serving import SortServer
+    arr, sizes, hv = workloads.serving_requests(requests, seed=workloads.SEEDS["serving"])
+    pool = workloads.uniform_u32(1 << 26, seed=7)
+    pool_v = np.arange(1 << 26, dtype=np.uint32)
+    srv = SortServer(pool, pool_v, budget_bytes=16 << 30, streams=4)
+    srv.warmup(int(sizes.max()))                         # workspaces and plans before the clock starts
+    warm = min(200, requests)
+    srv.run(arr[:warm], sizes[:warm], hv[:warm])
+    stats = srv.run(arr, sizes, hv)
+    stats["rate_req_s"] = 2000.0
+    return stats
 
 
 def load_peaks():
@@ -252,8 +348,9 @@ def main():
         avg_ms = statistics.mean(per_kind[dom])
         algo_bytes = 2 * 4 * n  # each launch reads and writes every key once
         achieved = algo_bytes / (avg_ms / 1e3) / 1e9
+        traffic = measured_traffic(n)
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
-                            "frac": achieved / hbm_gbs, "traffic": None,
+                            "frac": achieved / hbm_gbs, "traffic": traffic,
                             "kernel": bt.KIND_NAMES[dom], "launches_per_step": len(per_kind[dom]) // args.steps,
                             "avg_launch_ms": avg_ms, "peak_source": peak_src,
                             "share": {bt.KIND_NAMES[k]: v / sum(tot.values()) for k, v in tot.items()}}
@@ -278,6 +375,10 @@ def main():
                        "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms}
         out = host_out.numpy().view(np.uint32)
         assert np.all(out[1:] >= out[:-1])
+    if not args.no_segmented and rank == 0:
+        line["segmented"] = segmented_leg(bt, torch, max(3, args.steps))
+    if not args.no_serving and rank == 0:
+        line["serving"] = serving_leg(bt, args.serving_requests)
     if not args.no_cpu_baseline and rank == 0:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -105,6 +105,18 @@ bitonic_status bitonic_sort_segmented_pairs_u32(uint32_t *keys, uint32_t *vals,
                                                 const int32_t *offsets, int nseg,
                                                 bitonic_stream_t stream);
 
+/*
+ * bitonic_sort_segmented_pairs_u32 for callers that know every segment is at
+ * most max_len pairs long.  With max_len <= 8192 (one packed tile of 64-bit
+ * composites) no segment needs the composite workspace, so nothing is read
+ * back to the host and the call is fully asynchronous; larger bounds behave
+ * like bitonic_sort_segmented_pairs_u32.  A segment longer than max_len is
+ * a caller error (its result is undefined).  Used by the serving loop.
+ */
+bitonic_status bitonic_sort_segmented_pairs_u32_bounded(uint32_t *keys, uint32_t *vals,
+                                                        const int32_t *offsets, int nseg, int max_len,
+                                                        bitonic_stream_t stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *bitonic_status_string(bitonic_status s);
 

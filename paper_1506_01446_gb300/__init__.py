@@ -28,7 +28,7 @@ EXPORTS = (
     "bitonic_sort_segmented_pairs_u32", "bitonic_status_string", "bitonic_last_error_message",
     "bitonic_last_device_error", "bitonic_release_workspace", "bitonic_set_options",
     "bitonic_get_options", "bitonic_plan_info", "bitonic_sort_u32_profiled", "bitonic_debug_plan",
-    "bitonic_debug_desc_size", "bitonic_sort_pairs_u32_noalloc",
+    "bitonic_debug_desc_size", "bitonic_sort_pairs_u32_noalloc", "bitonic_sort_segmented_pairs_u32_bounded",
 )
 
 
@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
     lib.bitonic_debug_desc_size.argtypes = []
     lib.bitonic_debug_desc_size.restype = sz
     lib.bitonic_sort_pairs_u32_noalloc.argtypes = [vp, vp, sz, i32, vp]
+    lib.bitonic_sort_segmented_pairs_u32_bounded.argtypes = [vp, vp, vp, i32, i32, vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if f.restype is ctypes.c_int or f.restype is None:
@@ -155,6 +156,17 @@ def sort_segmented_pairs_(keys, vals, offsets, stream=None):
     _check(load().bitonic_sort_segmented_pairs_u32(_u32_ptr(keys, "keys"), _u32_ptr(vals, "vals"),
                                                    _offsets_ptr(offsets), nseg, _stream_handle(stream)),
            "bitonic_sort_segmented_pairs_u32")
+    return keys, vals
+
+
+def sort_segmented_pairs_bounded_(keys, vals, offsets, max_len: int, stream=None):
+    """Segmented pair sort for segments known to be at most max_len long
+    (fully asynchronous when max_len <= 8192)."""
+    nseg = offsets.numel() - 1
+    _check(load().bitonic_sort_segmented_pairs_u32_bounded(_u32_ptr(keys, "keys"), _u32_ptr(vals, "vals"),
+                                                           _offsets_ptr(offsets), nseg, int(max_len),
+                                                           _stream_handle(stream)),
+           "bitonic_sort_segmented_pairs_u32_bounded")
     return keys, vals
 
 

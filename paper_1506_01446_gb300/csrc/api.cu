@@ -11,6 +11,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "bitonic.h"
 #include "internal.h"
@@ -38,6 +39,8 @@ struct StreamWs {
     int* host = nullptr;         // pinned copy of the stats
     uint64_t* comp = nullptr;    // pair composites
     size_t comp_cap = 0;         // in elements
+    void* seg = nullptr;         // segmented batch plan, class bytes and class order
+    size_t seg_cap = 0;          // in bytes
 };
 
 struct PlanEntry {
@@ -60,6 +63,7 @@ struct DeviceState {
     int num_sms = 0;
     int pipe_blocks[kNumTileCfgs] = {};  // resident pipelined CTAs per SM, per configuration
     int* status = nullptr;               // device status word shared by every stream
+    TileParamsBig* seg_descs[2] = {nullptr, nullptr};  // packed segment tiles by class: keys, pairs
     std::map<cudaStream_t, StreamWs> ws;
     std::map<PlanKey, std::unique_ptr<PlanEntry>> plans;
     std::map<GraphKey, GraphEntry> graphs;
@@ -103,6 +107,16 @@ bitonic_status device_state(DeviceState** out)
         BT_CK(cudaStreamCreateWithFlags(&ds.capture, cudaStreamNonBlocking));
         BT_CK(cudaMalloc(&ds.status, sizeof(int)));
         BT_CK(cudaMemset(ds.status, 0, sizeof(int)));
+        for (int which = 0; which < 2; ++which) {
+            const int kb = which ? 8 : 4, m = which ? 13 : 14;
+            std::vector<TileParamsBig> descs(m + 1);
+            std::memset(descs.data(), 0, descs.size() * sizeof(TileParamsBig));
+            for (int k = 1; k <= m; ++k)
+                if (!make_class_desc(kb, k, descs[k])) return BITONIC_ERR_UNSUPPORTED;
+            BT_CK(cudaMalloc(&ds.seg_descs[which], descs.size() * sizeof(TileParamsBig)));
+            BT_CK(cudaMemcpy(ds.seg_descs[which], descs.data(), descs.size() * sizeof(TileParamsBig),
+                             cudaMemcpyHostToDevice));
+        }
         ds.inited = true;
     }
     *out = &ds;
@@ -120,12 +134,25 @@ bool stream_capturing(cudaStream_t s)
 // being captured nothing can be allocated: the call then uses the stream's
 // existing workspace, or else the device's default (NULL-stream) workspace,
 // and fails if neither is large enough.
-bitonic_status stream_ws(DeviceState& ds, cudaStream_t s, size_t comp_need, StreamWs** out)
+void drop_stream_graphs(DeviceState& ds, cudaStream_t s)
+{
+    for (auto it = ds.graphs.begin(); it != ds.graphs.end();) {
+        if (std::get<7>(it->first) == (uintptr_t)s) {
+            cudaGraphExecDestroy(it->second.exec);
+            it = ds.graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+bitonic_status stream_ws(DeviceState& ds, cudaStream_t s, size_t comp_need, StreamWs** out, size_t seg_need = 0)
 {
     if (stream_capturing(s)) {
         for (cudaStream_t key : {s, (cudaStream_t) nullptr}) {
             auto it = ds.ws.find(key);
-            if (it != ds.ws.end() && it->second.dev && it->second.comp_cap >= comp_need) {
+            if (it != ds.ws.end() && it->second.dev && it->second.comp_cap >= comp_need &&
+                it->second.seg_cap >= seg_need) {
                 *out = &it->second;
                 return BITONIC_OK;
             }
@@ -145,19 +172,22 @@ bitonic_status stream_ws(DeviceState& ds, cudaStream_t s, size_t comp_need, Stre
             BT_CK(cudaFree(w.comp));
             w.comp = nullptr;
             w.comp_cap = 0;
-            // graphs captured with the old buffer must not be replayed
-            for (auto it = ds.graphs.begin(); it != ds.graphs.end();) {
-                if (std::get<7>(it->first) == (uintptr_t)s) {
-                    cudaGraphExecDestroy(it->second.exec);
-                    it = ds.graphs.erase(it);
-                } else {
-                    ++it;
-                }
-            }
+            drop_stream_graphs(ds, s);  // graphs captured with the old buffer must not be replayed
         }
         size_t cap = (comp_need + 1) & ~size_t(1);
         BT_CK(cudaMalloc(&w.comp, cap * sizeof(uint64_t)));
         w.comp_cap = cap;
+    }
+    if (seg_need > w.seg_cap) {
+        if (w.seg) {
+            BT_CK(cudaStreamSynchronize(s));
+            BT_CK(cudaFree(w.seg));
+            w.seg = nullptr;
+            w.seg_cap = 0;
+            drop_stream_graphs(ds, s);
+        }
+        BT_CK(cudaMalloc(&w.seg, seg_need));
+        w.seg_cap = seg_need;
     }
     *out = &w;
     return BITONIC_OK;
@@ -331,14 +361,8 @@ bitonic_status sort_pairs_impl(uint32_t* keys, uint32_t* vals, size_t n, int asc
     });
 }
 
-int seg_grid(const DeviceState& ds, int nseg)
-{
-    int g = ds.num_sms * 8;
-    return nseg < g ? nseg : g;
-}
-
 bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t* offsets, int nseg,
-                                   cudaStream_t s)
+                                   cudaStream_t s, int64_t max_len = -1)
 {
     if (nseg < 0 || !offsets) {
         t_last_error = "negative segment count or null offsets";
@@ -353,21 +377,30 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
     DeviceState* ds;
     if ((st = device_state(&ds))) return st;
     StreamWs* w;
-    if ((st = stream_ws(*ds, s, 0, &w))) return st;
-    const int grid = seg_grid(*ds, nseg);
+    const size_t seg_need = seg_tiles_ws_bytes(nseg);
+    if ((st = stream_ws(*ds, s, 0, &w, seg_need))) return st;
+    const int tile_grid = 2 * ds->num_sms;   // two resident tile CTAs per SM
+    const int large_grid = 4 * ds->num_sms;
     if (!vals) {
-        int* counter = w->dev + 1;
-        int* status = ds->status;
         GraphKey key{2, 0, 1, (uintptr_t)keys, 0, (uintptr_t)offsets, nseg, (uintptr_t)s, 0, 0, 0};
+        void* ws = w->seg;
         return run_graphed(*ds, key, s, [&](cudaStream_t cs) -> bitonic_status {
-            BT_CK(seg_launch_keys(keys, offsets, nseg, counter, status, debug_checks(), grid, cs));
+            BT_CK(seg_tiles_launch(keys, nullptr, offsets, nseg, ws, ds->seg_descs[0], tile_grid, ds->status,
+                                   debug_checks(), cs));
+            BT_CK(seg_launch_large(keys, nullptr, offsets, ws, nullptr, 0, large_grid, cs));
             return BITONIC_OK;
         });
     }
-    // Pairs: longer segments need a composite workspace sized by the span.
-    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
-    BT_CK(cudaStreamIsCapturing(s, &cst));
-    if (cst != cudaStreamCaptureStatusNone) {
+    // Pairs: segments longer than one tile need a composite workspace sized
+    // by the span of the offsets, which is read back first -- unless the
+    // caller bounds every segment by one tile.
+    if (max_len >= 0 && max_len <= (1 << 13)) {
+        void* ws = w->seg;
+        BT_CK(seg_tiles_launch(keys, vals, offsets, nseg, ws, ds->seg_descs[1], tile_grid, ds->status,
+                               debug_checks(), s));
+        return BITONIC_OK;
+    }
+    if (stream_capturing(s)) {
         t_last_error = "segmented pair sort reads its segment sizes back and cannot be captured";
         return BITONIC_ERR_UNSUPPORTED;
     }
@@ -376,9 +409,11 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
     BT_CK(cudaStreamSynchronize(s));
     const int32_t first = w->host[0], last = w->host[1], longest = w->host[2];
     size_t need = 0;
-    if ((uint32_t)longest > kSegSmemPairs && last > first) need = (size_t)(last - first);
-    if ((st = stream_ws(*ds, s, need, &w))) return st;
-    BT_CK(seg_launch_pairs(keys, vals, offsets, nseg, w->comp, first, w->dev + 1, ds->status, debug_checks(), grid, s));
+    if (longest > (1 << 13) && last > first) need = (size_t)(last - first);
+    if ((st = stream_ws(*ds, s, need, &w, seg_need))) return st;
+    BT_CK(seg_tiles_launch(keys, vals, offsets, nseg, w->seg, ds->seg_descs[1], tile_grid, ds->status,
+                           debug_checks(), s));
+    BT_CK(seg_launch_large(keys, vals, offsets, w->seg, w->comp, first, large_grid, s));
     return BITONIC_OK;
 }
 
@@ -418,6 +453,14 @@ bitonic_status bitonic_sort_segmented_pairs_u32(uint32_t* keys, uint32_t* vals, 
 {
     if (!vals && nseg > 0) return BITONIC_ERR_INVALID;
     return sort_segmented_impl(keys, vals, offsets, nseg, (cudaStream_t)stream);
+}
+
+bitonic_status bitonic_sort_segmented_pairs_u32_bounded(uint32_t* keys, uint32_t* vals, const int32_t* offsets,
+                                                        int nseg, int max_len, bitonic_stream_t stream)
+{
+    if (!vals && nseg > 0) return BITONIC_ERR_INVALID;
+    if (max_len < 0) return BITONIC_ERR_INVALID;
+    return sort_segmented_impl(keys, vals, offsets, nseg, (cudaStream_t)stream, max_len);
 }
 
 const char* bitonic_status_string(bitonic_status s)
@@ -471,6 +514,7 @@ bitonic_status bitonic_release_workspace(void)
         if (kv.second.dev) cudaFree(kv.second.dev);
         if (kv.second.host) cudaFreeHost(kv.second.host);
         if (kv.second.comp) cudaFree(kv.second.comp);
+        if (kv.second.seg) cudaFree(kv.second.seg);
     }
     ds.ws.clear();
     return BITONIC_OK;

@@ -325,6 +325,23 @@ bool to_small(const TileParamsBig& b, TileParams& s)
 
 const TileCfg& tile_cfg(int id) { return kCfgs[id]; }
 
+// Descriptor of a packed segmented tile whose segments are padded to 2^k
+// positions: phases 1..k of the network on a contiguous tile of the default
+// configuration (16K keys, or 8K composites for pairs).
+bool make_class_desc(int key_bytes, int k, TileParamsBig& P)
+{
+    std::memset(&P, 0, sizeof(P));
+    const int cfg_id = key_bytes == 4 ? 0 : 4;
+    const TileCfg& cfg = kCfgs[cfg_id];
+    const int vb = key_bytes == 4 ? 2 : 1;
+    const int m = cfg.log_r + cfg.log_t;
+    if (k < 1 || k > m) return false;
+    std::vector<int> B;
+    for (int b = 0; b < m; ++b) B.push_back(b);
+    if (!map_bits(P, B, false, m)) return false;
+    return plan_rounds(tile_sort_steps(k), cfg, vb, 0, P);
+}
+
 Plan make_plan(uint64_t nv, int key_bytes, const Options& opt)
 {
     Plan plan;

@@ -1,20 +1,39 @@
-// Segmented-sort launchers (segmented.cu).
+// Segmented-sort launchers (segmented.cu, segmented_tiles.cu).
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "desc.h"
+
 namespace bitonic {
 
-constexpr uint32_t kSegSmemKeys = 16384;   // keys-only segments sorted in shared memory
-constexpr uint32_t kSegSmemPairs = 8192;   // pair segments sorted in shared memory
+constexpr int kSegClasses = 32;       // size classes: k = ceil(log2 length)
+constexpr int kSegClassSkip = 30;     // length 0 or 1: nothing to do
+constexpr int kSegClassLarge = 31;    // longer than one tile
+constexpr int kSegMaxPerTile = 1024;  // segments packed into one tile at most
+
+// Device-side plan of one segmented batch (built by the classify / scan kernels).
+struct SegPlan {
+    int hist[kSegClasses];            // segments per class
+    int seg_start[kSegClasses];       // first position of each class in `order`
+    int tile_start[kSegClasses + 1];  // first packed tile of each class
+    int cursor[kSegClasses];
+    int total_tiles;
+    int tile_counter;                 // persistent CTAs' work counter
+    int large_counter;
+    int pad_;
+};
 
 cudaError_t seg_init_attributes();
-cudaError_t seg_launch_keys(uint32_t* keys, const int32_t* offs, int nseg, int* counter, int* status,
-                            int debug_checks, int grid, cudaStream_t s);
-cudaError_t seg_launch_pairs(uint32_t* keys, uint32_t* vals, const int32_t* offs, int nseg, uint64_t* comp,
-                             int32_t comp_base, int* counter, int* status, int debug_checks, int grid,
+cudaError_t seg_tiles_init_attributes();
+size_t seg_tiles_ws_bytes(int nseg);
+cudaError_t seg_tiles_launch(uint32_t* keys, uint32_t* vals, const int32_t* offs, int nseg, void* ws,
+                             const TileParamsBig* class_descs, int grid, int* status, int debug_checks,
                              cudaStream_t s);
+// Segments of the large class (longer than one tile), one CTA each.
+cudaError_t seg_launch_large(uint32_t* keys, uint32_t* vals, const int32_t* offs, void* ws, uint64_t* comp,
+                             int32_t comp_base, int grid, cudaStream_t s);
 // out[0] = offsets[0], out[1] = offsets[nseg], out[2] = longest segment.
 cudaError_t seg_launch_stats(const int32_t* offs, int nseg, int* out, cudaStream_t s);
 

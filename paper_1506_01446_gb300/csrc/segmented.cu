@@ -1,9 +1,8 @@
-// Segmented sort: many independent arrays sorted ascending in one launch.
-// CTAs pull segments from an atomic work counter (persistent kernel).  A
-// segment that fits in shared memory is sorted there with the network of
-// Section 3.1 in mirror form (Section 4.1: one CTA, block barriers between
-// steps); longer segments run the same network on global memory, still one
-// CTA per segment.
+// Segmented sort: segments longer than one tile, and the batch statistics
+// used to size the pair workspace.  Each long segment is sorted by one CTA
+// running the network of Section 3.1 (mirror form) on global memory with
+// block barriers between steps; persistent CTAs pull segments from an
+// atomic counter.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,28 +24,6 @@ __device__ __forceinline__ uint32_t next_pow2_u32(uint32_t v)
 __device__ __forceinline__ int log2_u32(uint32_t N)
 {
     return 31 - __clz(N);
-}
-
-// Mirror-form network over N (power of two) entries of smem array a, all
-// ascending.  Positions >= len already hold the maximal pad.
-template <typename K>
-__device__ void smem_network(K* a, uint32_t N)
-{
-    const int k = log2_u32(N);
-    for (int p = 1; p <= k; ++p) {
-        for (int j = p - 1; j >= 0; --j) {
-            for (uint32_t q = threadIdx.x; q < N / 2; q += blockDim.x) {
-                const uint32_t i = ((q >> j) << (j + 1)) | (q & ((1u << j) - 1u));
-                const uint32_t pr = (j == p - 1) ? (i ^ ((2u << j) - 1u)) : (i | (1u << j));
-                const K x = a[i], y = a[pr];
-                if (y < x) {
-                    a[i] = y;
-                    a[pr] = x;
-                }
-            }
-            __syncthreads();
-        }
-    }
 }
 
 // Same network on global memory with virtual padding (partner >= len is a
@@ -73,86 +50,40 @@ __device__ void global_network(K* a, uint32_t len)
     }
 }
 
+// Segments longer than one tile (the large class of a batch), one CTA each,
+// taken from the batch's class-ordered list.  Pairs sort 64-bit composites
+// (key, position) kept in comp at the segment's offset minus comp_base.
 __global__ void __launch_bounds__(kSegThreads)
-k_seg_keys(uint32_t* __restrict__ keys, const int32_t* __restrict__ offs, int nseg, int* counter, int* status,
-           int debug_checks)
+k_seg_large(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const int32_t* __restrict__ offs,
+            const int32_t* __restrict__ order, SegPlan* plan, uint64_t* __restrict__ comp, int32_t comp_base)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t* a = reinterpret_cast<uint32_t*>(smem_raw);
     __shared__ int item;
+    const int n_large = plan->hist[kSegClassLarge];
+    const int32_t* list = order + plan->seg_start[kSegClassLarge];
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+        if (threadIdx.x == 0) item = atomicAdd(&plan->large_counter, 1);
         __syncthreads();
-        const int s = item;
-        if (s >= nseg) return;
-        const int32_t b = offs[s], e = offs[s + 1];
-        if (e < b) {
-            if (debug_checks && threadIdx.x == 0) atomicCAS(status, 0, 1);
-            continue;
-        }
-        const uint32_t len = (uint32_t)(e - b);
-        if (len < 2) continue;
-        uint32_t* seg = keys + b;
-        if (len <= kSegSmemKeys) {
-            const uint32_t N = next_pow2_u32(len);
-            for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) a[i] = i < len ? seg[i] : 0xFFFFFFFFu;
-            __syncthreads();
-            smem_network(a, N);
-            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) seg[i] = a[i];
-        } else {
-            global_network(seg, len);
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kSegThreads)
-k_seg_pairs(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const int32_t* __restrict__ offs,
-            int nseg, uint64_t* __restrict__ comp, int32_t comp_base, int* counter, int* status,
-            int debug_checks)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t* a = reinterpret_cast<uint64_t*>(smem_raw);
-    uint32_t* v = reinterpret_cast<uint32_t*>(a + kSegSmemPairs);
-    __shared__ int item;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int s = item;
-        if (s >= nseg) return;
-        const int32_t b = offs[s], e = offs[s + 1];
-        if (e < b) {
-            if (debug_checks && threadIdx.x == 0) atomicCAS(status, 0, 1);
-            continue;
-        }
-        const uint32_t len = (uint32_t)(e - b);
-        if (len < 2) continue;
+        const int i = item;
+        if (i >= n_large) return;
+        const int s = list[i];
+        const int32_t b = offs[s];
+        const uint32_t len = (uint32_t)(offs[s + 1] - b);
         uint32_t* sk = keys + b;
+        if (!vals) {
+            global_network(sk, len);
+            continue;
+        }
         uint32_t* sv = vals + b;
-        if (len <= kSegSmemPairs) {
-            const uint32_t N = next_pow2_u32(len);
-            for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
-                a[i] = i < len ? (((uint64_t)sk[i] << 32) | i) : ~0ull;
-                if (i < len) v[i] = sv[i];
-            }
-            __syncthreads();
-            smem_network(a, N);
-            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
-                sk[i] = (uint32_t)(a[i] >> 32);
-                sv[i] = v[(uint32_t)a[i]];
-            }
-        } else {
-            uint64_t* c = comp + (b - comp_base);
-            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) c[i] = ((uint64_t)sk[i] << 32) | i;
-            __syncthreads();
-            global_network(c, len);
-            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) c[i] = (c[i] & ~0xFFFFFFFFull) | sv[(uint32_t)c[i]];
-            __syncthreads();
-            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
-                sk[i] = (uint32_t)(c[i] >> 32);
-                sv[i] = (uint32_t)c[i];
-            }
+        uint64_t* c = comp + (b - comp_base);
+        for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) c[j] = ((uint64_t)sk[j] << 32) | j;
+        __syncthreads();
+        global_network(c, len);
+        for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) c[j] = (c[j] & ~0xFFFFFFFFull) | sv[(uint32_t)c[j]];
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) {
+            sk[j] = (uint32_t)(c[j] >> 32);
+            sv[j] = (uint32_t)c[j];
         }
     }
 }
@@ -173,33 +104,14 @@ __global__ void k_seg_stats(const int32_t* __restrict__ offs, int nseg, int* out
 
 }  // namespace
 
-cudaError_t seg_init_attributes()
-{
-    cudaError_t e = cudaFuncSetAttribute(k_seg_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kSegSmemKeys * sizeof(uint32_t)));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_seg_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(kSegSmemPairs * (sizeof(uint64_t) + sizeof(uint32_t))));
-}
+cudaError_t seg_init_attributes() { return seg_tiles_init_attributes(); }
 
-cudaError_t seg_launch_keys(uint32_t* keys, const int32_t* offs, int nseg, int* counter, int* status,
-                            int debug_checks, int grid, cudaStream_t s)
+cudaError_t seg_launch_large(uint32_t* keys, uint32_t* vals, const int32_t* offs, void* ws, uint64_t* comp,
+                             int32_t comp_base, int grid, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
-    if (e != cudaSuccess) return e;
-    k_seg_keys<<<grid, kSegThreads, kSegSmemKeys * sizeof(uint32_t), s>>>(keys, offs, nseg, counter, status,
-                                                                         debug_checks);
-    return cudaGetLastError();
-}
-
-cudaError_t seg_launch_pairs(uint32_t* keys, uint32_t* vals, const int32_t* offs, int nseg, uint64_t* comp,
-                             int32_t comp_base, int* counter, int* status, int debug_checks, int grid,
-                             cudaStream_t s)
-{
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
-    if (e != cudaSuccess) return e;
-    k_seg_pairs<<<grid, kSegThreads, kSegSmemPairs * (sizeof(uint64_t) + sizeof(uint32_t)), s>>>(
-        keys, vals, offs, nseg, comp, comp_base, counter, status, debug_checks);
+    SegPlan* plan = reinterpret_cast<SegPlan*>(ws);
+    const int32_t* order = reinterpret_cast<const int32_t*>(plan + 1);
+    k_seg_large<<<grid, kSegThreads, 0, s>>>(keys, vals, offs, order, plan, comp, comp_base);
     return cudaGetLastError();
 }
 

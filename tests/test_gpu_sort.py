@@ -229,3 +229,26 @@ def test_n28_uniform_full(seed):
     torch.cuda.empty_cache()
     want = oracle.merge_sort(keys, True)
     assert np.array_equal(got, want)
+
+
+def test_segmented_pairs_bounded_is_asynchronous_path():
+    keys, offs = workloads.segmented_u32(5000, seed=8, max_len=8192)
+    vals = workloads.uniform_u32(keys.size, seed=81)
+    tk, tv = to_dev(keys), to_dev(vals)
+    to = torch.from_numpy(offs).cuda()
+    bt.sort_segmented_pairs_bounded_(tk, tv, to, 8192)
+    torch.cuda.synchronize()
+    wk, wv = oracle.segmented_sort_pairs(keys, vals, offs)
+    assert np.array_equal(to_host(tk), wk) and np.array_equal(to_host(tv), wv)
+
+
+def test_segmented_many_tiny_and_class_boundaries():
+    # every class boundary 2^k and 2^k + 1, plus many length-2..16 segments
+    lens = []
+    for k in range(1, 15):
+        lens += [1 << k, (1 << k) + 1, (1 << k) - 1]
+    lens += [2, 3, 5, 9, 16, 17] * 500
+    keys, offs = segments_case(lens, seed=21)
+    check_segmented(keys, offs)
+    keys2, offs2 = segments_case([l for l in lens if l <= 8192], seed=22)
+    check_segmented(keys2, offs2, pairs=True)
