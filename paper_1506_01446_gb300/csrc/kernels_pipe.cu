@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "engine.cuh"
+#include "tile_pass.cuh"
 #include "kernel_cfg.h"
 #include "tma.cuh"
 
@@ -37,7 +38,7 @@ __device__ __forceinline__ uint32_t row_global(const PT& P, int c, uint32_t r)
     return g;
 }
 
-template <int ASYNC, typename K, bool DESC, int LOG_R, int LOG_T, class PT>
+template <int ASYNC, bool CATALOG, typename K, bool DESC, int LOG_R, int LOG_T, class PT>
 __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uint32_t hi, const PT& P,
                                           uint32_t ntiles, K cm_in, K cm_out, int* status)
 {
@@ -154,15 +155,7 @@ __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uin
         if (x == 0) *fill_count = 0;
         __syncthreads();
         if (next < ntiles) issue(next);
-        run_round_steps<DESC>(t.r, P.rounds[0]);
-        const int nr = P.nrounds;
-        for (int rd = 1; rd < nr; ++rd) {
-            if (rd > 1) __syncthreads();
-            t.smem_write(Y, P.rounds[rd - 1], x);
-            __syncthreads();
-            t.smem_read(Y, P.rounds[rd], x);
-            run_round_steps<DESC>(t.r, P.rounds[rd]);
-        }
+        run_tile_rounds<K, DESC, LOG_R, LOG_T, CATALOG>(t, Y, P, x);
         t.store_global(base, lo, hi, P.io[1], g0, x, cm_out);
         __syncthreads();
     }
@@ -173,7 +166,7 @@ __global__ void __launch_bounds__(1 << LOG_T)
 k_pipe(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P, uint32_t ntiles,
        K cm_in, K cm_out, int* status)
 {
-    pipe_pass<ASYNC, K, false, LOG_R, LOG_T>(base, lo, hi, P, ntiles, cm_in, cm_out, status);
+    pipe_pass<ASYNC, false, K, false, LOG_R, LOG_T>(base, lo, hi, P, ntiles, cm_in, cm_out, status);
 }
 
 template <int ASYNC, typename K, int LOG_R, int LOG_T>
@@ -181,7 +174,7 @@ __global__ void __launch_bounds__(1 << LOG_T)
 k_pipe_big(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParamsBig* __restrict__ P, uint32_t ntiles,
            K cm_in, K cm_out, int* status)
 {
-    pipe_pass<ASYNC, K, false, LOG_R, LOG_T>(base, lo, hi, *P, ntiles, cm_in, cm_out, status);
+    pipe_pass<ASYNC, false, K, false, LOG_R, LOG_T>(base, lo, hi, *P, ntiles, cm_in, cm_out, status);
 }
 
 template <typename K, int LR, int LT>

@@ -65,6 +65,30 @@ __device__ __forceinline__ void middle_round(typename Tile<K, DESC, LOG_R, LOG_T
     }
 }
 
+// The rounds of one tile once round 0's keys are in t's registers: round 0's
+// steps, then each later round's shared-memory transpose and steps (Section
+// 4.1 between rounds, Section 4.2 within them).  Leaves the last round's
+// keys in t's registers.
+template <typename K, bool DESC, int LOG_R, int LOG_T, bool CATALOG, class PT>
+__device__ __forceinline__ void run_tile_rounds(Tile<K, DESC, LOG_R, LOG_T>& t,
+                                                typename Tile<K, DESC, LOG_R, LOG_T>::Vec* sm, const PT& P,
+                                                uint32_t x)
+{
+    constexpr int kCat = CATALOG ? LOG_R : 0;  // catalog_size(0) == 0: per-step dispatch only
+    const int nr = P.nrounds;
+    steps_in_place<kCat, DESC>(t.r, P.rounds[0]);
+    if (nr > 1) {
+        t.smem_write(sm, P.rounds[0], x);
+        for (int rd = 1; rd < nr - 1; ++rd) {
+            __syncthreads();
+            middle_round<K, DESC, LOG_R, LOG_T, CATALOG>(sm, P.rounds[rd], x);
+        }
+        __syncthreads();
+        t.smem_read(sm, P.rounds[nr - 1], x);
+        steps_in_place<kCat, DESC>(t.r, P.rounds[nr - 1]);
+    }
+}
+
 // One tile pass (Sections 4.1 and 4.2): load a tile of 2^m keys, run the
 // rounds (register network steps, shared-memory transposes in between), store.
 template <typename K, bool DESC, int LOG_R, int LOG_T, bool CATALOG, class PT>
@@ -78,24 +102,12 @@ __device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uin
     const uint32_t g0 = cta_base(P, blockIdx.x);
     if (P.contiguous && g0 >= hi) return;  // the whole tile is tail padding
     const bool interior = (g0 & ~P.span_mask) >= lo && (g0 | P.span_mask) < hi;
-    const int nr = P.nrounds;
     T t;
     if (interior)
         t.load_global_interior(base, P.io[0], g0, x, cm_in);
     else
         t.load_global(base, lo, hi, P.io[0], g0, x, cm_in);
-    constexpr int kCat = CATALOG ? LOG_R : 0;  // catalog_size(0) == 0: per-step dispatch only
-    steps_in_place<kCat, DESC>(t.r, P.rounds[0]);
-    if (nr > 1) {
-        t.smem_write(sm, P.rounds[0], x);
-        for (int rd = 1; rd < nr - 1; ++rd) {
-            __syncthreads();
-            middle_round<K, DESC, LOG_R, LOG_T, CATALOG>(sm, P.rounds[rd], x);
-        }
-        __syncthreads();
-        t.smem_read(sm, P.rounds[nr - 1], x);
-        steps_in_place<kCat, DESC>(t.r, P.rounds[nr - 1]);
-    }
+    run_tile_rounds<K, DESC, LOG_R, LOG_T, CATALOG>(t, sm, P, x);
     if (interior)
         t.store_global_interior(base, P.io[1], g0, x, cm_out);
     else
