@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-segmented", action="store_true", help="skip the batched segmented leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop leg")
     ap.add_argument("--serving-requests", type=int, default=20000)
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     return ap.parse_args()
 
 
@@ -272,6 +273,13 @@ def main():
     n = 1 << args.n_log2
     hbm_gbs, peak_src = load_peaks()
     keys_np = workloads.uniform_u32(n, seed=workloads.SEEDS["n28_uniform"] + rank)
+    tuned = None
+    if not args.no_tune:
+        import tempfile
+        from paper_1506_01446_gb300 import autotune
+        tuned = autotune.tune(classes=(args.n_log2,), pair_classes=(), reps=3,
+                              cache_path=os.path.join(tempfile.gettempdir(), f"bitonic_tune_{rank}.json"))
+        tuned = {k: v for k, v in tuned["uint32"].get(str(args.n_log2), {}).items() if k != "tried"}
     pristine = torch.from_numpy(keys_np.view(np.int32)).cuda()
     buf = pristine.clone()
     stream = torch.cuda.current_stream()
@@ -317,7 +325,7 @@ def main():
         "config": {"workload": f"single uint32 array, n=2^{args.n_log2}, uniform random, ascending",
                    "n": n, "l2": "inputs larger than L2 (1 GiB per array)" if n >= 1 << 26 else
                    "input restored by a copy before each step", "parallelism": f"replicas x{world}",
-                   "plan": info},
+                   "plan": info, "tuned": tuned},
         "gpu_launches": info["launches"] * args.steps,
         "clocks": clk.summary(),
     }

@@ -164,6 +164,17 @@ bitonic_status bitonic_set_options(const bitonic_options *opt);
 bitonic_status bitonic_get_options(bitonic_options *opt);
 
 /*
+ * Tuned choice for one size class: sorts of N = 2^log2_n keys of key_bytes
+ * bytes (4: bitonic_sort_u32, 8: the composites of bitonic_sort_pairs_u32)
+ * use opt's tile_log2, keys_per_thread_log2, global_bits and pipeline
+ * instead of the process-wide values (the other fields are ignored).
+ * opt == NULL removes the class's choice.  Written by the autotuner
+ * (paper_1506_01446_gb300.autotune); BITONIC_ERR_UNSUPPORTED if the planner
+ * rejects the choice for that class.
+ */
+bitonic_status bitonic_set_class_options(int key_bytes, int log2_n, const bitonic_options *opt);
+
+/*
  * Describes the launch sequence bitonic_sort_u32 (pairs != 0: the composite
  * sort of bitonic_sort_pairs_u32) would run for n under the current options:
  * *launches = kernel launches, *hbm_passes = passes that read and write every

@@ -29,6 +29,7 @@ EXPORTS = (
     "bitonic_last_device_error", "bitonic_release_workspace", "bitonic_set_options",
     "bitonic_get_options", "bitonic_plan_info", "bitonic_sort_u32_profiled", "bitonic_debug_plan",
     "bitonic_debug_desc_size", "bitonic_sort_pairs_u32_noalloc", "bitonic_sort_segmented_pairs_u32_bounded",
+    "bitonic_set_class_options",
 )
 
 
@@ -78,6 +79,7 @@ def load() -> ctypes.CDLL:
     lib.bitonic_debug_desc_size.restype = sz
     lib.bitonic_sort_pairs_u32_noalloc.argtypes = [vp, vp, sz, i32, vp]
     lib.bitonic_sort_segmented_pairs_u32_bounded.argtypes = [vp, vp, vp, i32, i32, vp]
+    lib.bitonic_set_class_options.argtypes = [i32, i32, ctypes.POINTER(Options)]
     for name in EXPORTS:
         f = getattr(lib, name)
         if f.restype is ctypes.c_int or f.restype is None:
@@ -195,6 +197,15 @@ def set_options(variant=None, tile_log2=None, global_bits=None, use_graph=None,
             cur[k] = int(v)
     _check(load().bitonic_set_options(ctypes.byref(Options(**cur))), "bitonic_set_options")
     return cur
+
+
+def set_class_options(key_bytes: int, log2_n: int, options: dict | None):
+    """Installs (or with None removes) the tuned options of one size class."""
+    ptr = None
+    if options is not None:
+        o = Options(**{**{f: 0 for f, _ in Options._fields_}, **options})
+        ptr = ctypes.byref(o)
+    _check(load().bitonic_set_class_options(int(key_bytes), int(log2_n), ptr), "bitonic_set_class_options")
 
 
 def plan_info(n: int, pairs: bool = False) -> dict:

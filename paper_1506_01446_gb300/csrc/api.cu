@@ -45,8 +45,33 @@ struct StreamWs {
 
 struct PlanEntry {
     Plan plan;
+    Options opt;                       // options the plan was built with
     TileParamsBig* d_descs = nullptr;  // device copies, used by launches too big to pass by value
 };
+
+// Per-size-class overrides set by the autotuner: (key bytes, log2 N) -> options.
+std::map<std::pair<int, int>, Options> g_class_opt;
+
+// Options for a sort of N = 2^k keys of key_bytes bytes: the size class's
+// tuned choice of tile, keys per thread and strides per pass where one is
+// set, the process-wide options otherwise.
+Options resolve_options(int key_bytes, int k)
+{
+    auto it = g_class_opt.find({key_bytes, k});
+    if (it == g_class_opt.end() || g_opt.variant != 0) return g_opt;
+    Options o = g_opt;
+    o.tile_log2 = it->second.tile_log2;
+    o.keys_per_thread_log2 = it->second.keys_per_thread_log2;
+    o.global_bits = it->second.global_bits;
+    o.pipeline = it->second.pipeline;
+    return o;
+}
+
+int options_code(const Options& o)
+{
+    return ((o.variant * 16 + o.tile_log2) * 16 + o.keys_per_thread_log2) * 64 * 8 + o.global_bits * 8 +
+           o.io_direct * 2 + (o.pipeline ? 1 : 0) + o.pipeline * 4096 * 64;
+}
 
 using PlanKey = std::tuple<uint64_t, int, int, int, int, int, int>;
 // op, n, ascending, ptr a, ptr b, ptr c, count, stream, variant, tile, gbits
@@ -196,13 +221,15 @@ bitonic_status stream_ws(DeviceState& ds, cudaStream_t s, size_t comp_need, Stre
 bitonic_status get_plan(DeviceState& ds, uint64_t nv, int key_bytes, PlanEntry** out)
 {
     uint64_t N = 2;
-    while (N < nv) N <<= 1;
-    PlanKey key{N, key_bytes, g_opt.variant, g_opt.tile_log2, g_opt.global_bits, g_opt.keys_per_thread_log2,
-                g_opt.io_direct};
+    int k = 1;
+    while (N < nv) { N <<= 1; ++k; }
+    const Options o = resolve_options(key_bytes, k);
+    PlanKey key{N, key_bytes, o.variant, o.tile_log2, o.global_bits, o.keys_per_thread_log2, o.io_direct};
     auto it = ds.plans.find(key);
     if (it == ds.plans.end()) {
         auto pe = std::make_unique<PlanEntry>();
-        pe->plan = make_plan(N, key_bytes, g_opt);
+        pe->opt = o;
+        pe->plan = make_plan(N, key_bytes, o);
         if (!pe->plan.ok) {
             t_last_error = "planner could not schedule this size";
             return BITONIC_ERR_UNSUPPORTED;
@@ -245,10 +272,10 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
             // first load and the last store.
             const int cin = desc && i == 0, cout = desc && i + 1 == pl.launches.size();
             const int per_sm = ds.pipe_blocks[pl.cfg];
-            if (g_opt.pipeline && per_sm > 0 && status) {
+            if (pe.opt.pipeline && per_sm > 0 && status) {
                 uint64_t g = (uint64_t)per_sm * ds.num_sms;
                 const uint32_t grid = (uint32_t)(g < ntiles ? g : ntiles);
-                e = launch_pipe(g_opt.pipeline, pl.cfg, base, lo, hi, hP, dP, ntiles, grid, cin, cout, status, s);
+                e = launch_pipe(pe.opt.pipeline, pl.cfg, base, lo, hi, hP, dP, ntiles, grid, cin, cout, status, s);
             } else {
                 e = launch_tile(pl.cfg, base, lo, hi, hP, dP, ntiles, cin, cout, s);
             }
@@ -326,8 +353,7 @@ bitonic_status sort_u32_impl(uint32_t* keys, size_t n, int ascending, cudaStream
         if (nevents < (int)pe->plan.launches.size() + 1) return BITONIC_ERR_INVALID;
         return enqueue_plan(*ds, *pe, base, front, (uint32_t)nv, desc, 4, status, s, events, kinds);
     }
-    GraphKey key{0, n, desc, (uintptr_t)keys, 0, 0, 0, 0, g_opt.variant,
-                 g_opt.tile_log2 * 16 + g_opt.keys_per_thread_log2, g_opt.global_bits * 16 + g_opt.io_direct * 2 + g_opt.pipeline};
+    GraphKey key{0, n, desc, (uintptr_t)keys, 0, 0, 0, 0, 0, options_code(pe->opt), 0};
     return run_graphed(*ds, key, s, [&](cudaStream_t cs) {
         return enqueue_plan(*ds, *pe, base, front, (uint32_t)nv, desc, 4, status, cs, nullptr, nullptr);
     });
@@ -349,8 +375,8 @@ bitonic_status sort_pairs_impl(uint32_t* keys, uint32_t* vals, size_t n, int asc
     const int desc = ascending ? 0 : 1;
     const uint32_t nn = (uint32_t)n;
     uint64_t* comp = w->comp;
-    GraphKey key{1, n, desc, (uintptr_t)keys, (uintptr_t)vals, (uintptr_t)comp, 0, (uintptr_t)s, g_opt.variant,
-                 g_opt.tile_log2 * 16 + g_opt.keys_per_thread_log2, g_opt.global_bits * 16 + g_opt.io_direct * 2 + g_opt.pipeline};
+    GraphKey key{1, n, desc, (uintptr_t)keys, (uintptr_t)vals, (uintptr_t)comp, 0, (uintptr_t)s, 0,
+                 options_code(pe->opt), 0};
     return run_graphed(*ds, key, s, [&](cudaStream_t cs) -> bitonic_status {
         BT_CK(launch_pairs_pack(comp, keys, nn, desc, cs));
         bitonic_status st2 = enqueue_plan(*ds, *pe, comp, 0, nn, 0, 8, ds->status, cs, nullptr, nullptr);
@@ -539,6 +565,35 @@ bitonic_status bitonic_set_options(const bitonic_options* opt)
     return BITONIC_OK;
 }
 
+bitonic_status bitonic_set_class_options(int key_bytes, int log2_n, const bitonic_options* opt)
+{
+    if ((key_bytes != 4 && key_bytes != 8) || log2_n < 1 || log2_n > 31) return BITONIC_ERR_INVALID;
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!opt) {
+        g_class_opt.erase({key_bytes, log2_n});
+        return BITONIC_OK;
+    }
+    if (opt->tile_log2 != 0 && (opt->tile_log2 < 12 || opt->tile_log2 > 15)) return BITONIC_ERR_INVALID;
+    if (opt->keys_per_thread_log2 != 0 && (opt->keys_per_thread_log2 < 2 || opt->keys_per_thread_log2 > 7))
+        return BITONIC_ERR_INVALID;
+    if (opt->global_bits < 0 || opt->global_bits > 16 || opt->pipeline < 0 || opt->pipeline > 2)
+        return BITONIC_ERR_INVALID;
+    Options o;
+    o.tile_log2 = opt->tile_log2;
+    o.keys_per_thread_log2 = opt->keys_per_thread_log2;
+    o.global_bits = opt->global_bits;
+    o.pipeline = opt->pipeline;
+    // the planner must accept the choice for this class
+    Options probe = g_opt;
+    probe.variant = 0;
+    probe.tile_log2 = o.tile_log2;
+    probe.keys_per_thread_log2 = o.keys_per_thread_log2;
+    probe.global_bits = o.global_bits;
+    if (!make_plan(uint64_t(1) << log2_n, key_bytes, probe).ok) return BITONIC_ERR_UNSUPPORTED;
+    g_class_opt[{key_bytes, log2_n}] = o;
+    return BITONIC_OK;
+}
+
 bitonic_status bitonic_get_options(bitonic_options* opt)
 {
     if (!opt) return BITONIC_ERR_INVALID;
@@ -557,7 +612,14 @@ bitonic_status bitonic_plan_info(size_t n, int pairs, int* launches, int* hbm_pa
                                  int* global_steps)
 {
     if (n > kMaxKeys) return BITONIC_ERR_UNSUPPORTED;
-    Options o = current_options();
+    Options o;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        uint64_t N = 2;
+        int k = 1;
+        while (N < n) { N <<= 1; ++k; }
+        o = resolve_options(pairs ? 8 : 4, k);
+    }
     if (n <= 1) {
         if (launches) *launches = 0;
         if (hbm_passes) *hbm_passes = 0;
