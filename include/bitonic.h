@@ -154,12 +154,14 @@ typedef struct {
     int io_direct;        /* bit 0: load a tile straight into its first round's register layout,
                              bit 1: store straight from its last round's layout (instead of an
                              extra shared-memory transpose into a coalesced layout); 0 = off */
+    int l2_prefetch;      /* > 0: each tile CTA asks the TMA unit to prefetch into L2 the tile
+                             that many resident waves ahead (default 1); 0 = off */
     int pipeline;         /* 0 = one CTA per tile (default); persistent CTAs that prefetch the
                              next tile into shared memory with 1 = TMA bulk copies per row,
                              2 = per-thread 16-byte cp.async copies */
 } bitonic_options;
 
-/* Process-wide options (defaults: all zero except use_graph = 1). */
+/* Process-wide options (defaults: all zero except use_graph = 1 and l2_prefetch = 1). */
 bitonic_status bitonic_set_options(const bitonic_options *opt);
 bitonic_status bitonic_get_options(bitonic_options *opt);
 

@@ -2,8 +2,9 @@
 the fastest.
 
 A candidate is a tile size (tile_log2), keys held per thread in registers
-(keys_per_thread_log2) and the fused-stride cutoff (global_bits: the most
-strides at or above the tile size one pass may take; 0 = as many as fit).
+(keys_per_thread_log2), the fused-stride cutoff (global_bits: the most
+strides at or above the tile size one pass may take; 0 = as many as fit) and
+the L2 prefetch distance (l2_prefetch, in resident waves).
 For every size class 2^k the tuner times each candidate with CUDA events on
 data already in device memory, picks the fastest, installs it with
 bitonic_set_class_options and caches the choices as JSON per GPU name (path:
@@ -19,15 +20,15 @@ import statistics
 from . import set_class_options, sort_, sort_pairs_
 
 CANDIDATES_U32 = (
-    dict(tile_log2=14, keys_per_thread_log2=6, global_bits=0),
-    dict(tile_log2=14, keys_per_thread_log2=6, global_bits=8),
-    dict(tile_log2=13, keys_per_thread_log2=5, global_bits=0),
-    dict(tile_log2=14, keys_per_thread_log2=5, global_bits=0),
+    dict(tile_log2=14, keys_per_thread_log2=6, global_bits=0, l2_prefetch=1),
+    dict(tile_log2=14, keys_per_thread_log2=6, global_bits=8, l2_prefetch=1),
+    dict(tile_log2=14, keys_per_thread_log2=6, global_bits=8, l2_prefetch=0),
+    dict(tile_log2=13, keys_per_thread_log2=5, global_bits=0, l2_prefetch=1),
 )
 CANDIDATES_PAIRS = (
-    dict(tile_log2=13, keys_per_thread_log2=5, global_bits=0),
-    dict(tile_log2=13, keys_per_thread_log2=5, global_bits=7),
-    dict(tile_log2=12, keys_per_thread_log2=4, global_bits=0),
+    dict(tile_log2=13, keys_per_thread_log2=5, global_bits=0, l2_prefetch=1),
+    dict(tile_log2=13, keys_per_thread_log2=5, global_bits=7, l2_prefetch=1),
+    dict(tile_log2=12, keys_per_thread_log2=4, global_bits=0, l2_prefetch=1),
 )
 
 
@@ -105,7 +106,7 @@ def install(choices: dict) -> int:
     count = 0
     for kind, kb in (("uint32", 4), ("pairs", 8)):
         for k, c in choices.get(kind, {}).items():
-            opts = {f: c[f] for f in ("tile_log2", "keys_per_thread_log2", "global_bits") if f in c}
+            opts = {f: c[f] for f in ("tile_log2", "keys_per_thread_log2", "global_bits", "l2_prefetch") if f in c}
             set_class_options(kb, int(k), opts)
             count += 1
     return count

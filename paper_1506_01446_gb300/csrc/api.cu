@@ -64,16 +64,17 @@ Options resolve_options(int key_bytes, int k)
     o.keys_per_thread_log2 = it->second.keys_per_thread_log2;
     o.global_bits = it->second.global_bits;
     o.pipeline = it->second.pipeline;
+    o.l2_prefetch = it->second.l2_prefetch;
     return o;
 }
 
 int options_code(const Options& o)
 {
-    return ((o.variant * 16 + o.tile_log2) * 16 + o.keys_per_thread_log2) * 64 * 8 + o.global_bits * 8 +
-           o.io_direct * 2 + (o.pipeline ? 1 : 0) + o.pipeline * 4096 * 64;
+    return ((((o.variant * 16 + o.tile_log2) * 16 + o.keys_per_thread_log2) * 32 + o.global_bits) * 4 +
+            o.io_direct) * 64 + o.pipeline * 16 + o.l2_prefetch;
 }
 
-using PlanKey = std::tuple<uint64_t, int, int, int, int, int, int>;
+using PlanKey = std::tuple<uint64_t, int, int>;  // N, key bytes, options_code
 // op, n, ascending, ptr a, ptr b, ptr c, count, stream, variant, tile, gbits
 using GraphKey = std::tuple<int, uint64_t, int, uintptr_t, uintptr_t, uintptr_t, int, uintptr_t, int, int, int>;
 
@@ -87,6 +88,7 @@ struct DeviceState {
     cudaStream_t capture = nullptr;
     int num_sms = 0;
     int pipe_blocks[kNumTileCfgs] = {};  // resident pipelined CTAs per SM, per configuration
+    int tile_blocks[kNumTileCfgs] = {};  // resident tile CTAs per SM, per configuration
     int* status = nullptr;               // device status word shared by every stream
     TileParamsBig* seg_descs[2] = {nullptr, nullptr};  // packed segment tiles by class: keys, pairs
     std::map<cudaStream_t, StreamWs> ws;
@@ -128,6 +130,7 @@ bitonic_status device_state(DeviceState** out)
         BT_CK(cudaDeviceGetAttribute(&ds.num_sms, cudaDevAttrMultiProcessorCount, dev));
         BT_CK(init_tile_attributes());
         BT_CK(init_pipe_attributes(ds.pipe_blocks));
+        for (int c = 0; c < kNumTileCfgs; ++c) BT_CK(tile_blocks_per_sm(c, &ds.tile_blocks[c]));
         BT_CK(seg_init_attributes());
         BT_CK(cudaStreamCreateWithFlags(&ds.capture, cudaStreamNonBlocking));
         BT_CK(cudaMalloc(&ds.status, sizeof(int)));
@@ -224,7 +227,7 @@ bitonic_status get_plan(DeviceState& ds, uint64_t nv, int key_bytes, PlanEntry**
     int k = 1;
     while (N < nv) { N <<= 1; ++k; }
     const Options o = resolve_options(key_bytes, k);
-    PlanKey key{N, key_bytes, o.variant, o.tile_log2, o.global_bits, o.keys_per_thread_log2, o.io_direct};
+    PlanKey key{N, key_bytes, options_code(o)};
     auto it = ds.plans.find(key);
     if (it == ds.plans.end()) {
         auto pe = std::make_unique<PlanEntry>();
@@ -277,7 +280,10 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
                 const uint32_t grid = (uint32_t)(g < ntiles ? g : ntiles);
                 e = launch_pipe(pe.opt.pipeline, pl.cfg, base, lo, hi, hP, dP, ntiles, grid, cin, cout, status, s);
             } else {
-                e = launch_tile(pl.cfg, base, lo, hi, hP, dP, ntiles, cin, cout, s);
+                const uint32_t pf = pe.opt.l2_prefetch > 0
+                                        ? (uint32_t)(pe.opt.l2_prefetch * ds.tile_blocks[pl.cfg] * ds.num_sms)
+                                        : 0u;
+                e = launch_tile(pl.cfg, base, lo, hi, hP, dP, ntiles, cin, cout, s, pf);
             }
         }
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -562,6 +568,7 @@ bitonic_status bitonic_set_options(const bitonic_options* opt)
     g_opt.keys_per_thread_log2 = opt->keys_per_thread_log2;
     g_opt.pipeline = (opt->pipeline >= 0 && opt->pipeline <= 2) ? opt->pipeline : 0;
     g_opt.io_direct = opt->io_direct & 3;
+    g_opt.l2_prefetch = opt->l2_prefetch < 0 ? 0 : (opt->l2_prefetch > 8 ? 8 : opt->l2_prefetch);
     return BITONIC_OK;
 }
 
@@ -583,6 +590,7 @@ bitonic_status bitonic_set_class_options(int key_bytes, int log2_n, const bitoni
     o.keys_per_thread_log2 = opt->keys_per_thread_log2;
     o.global_bits = opt->global_bits;
     o.pipeline = opt->pipeline;
+    o.l2_prefetch = opt->l2_prefetch < 0 ? 0 : (opt->l2_prefetch > 8 ? 8 : opt->l2_prefetch);
     // the planner must accept the choice for this class
     Options probe = g_opt;
     probe.variant = 0;
@@ -605,6 +613,7 @@ bitonic_status bitonic_get_options(bitonic_options* opt)
     opt->keys_per_thread_log2 = g_opt.keys_per_thread_log2;
     opt->pipeline = g_opt.pipeline;
     opt->io_direct = g_opt.io_direct;
+    opt->l2_prefetch = g_opt.l2_prefetch;
     return BITONIC_OK;
 }
 

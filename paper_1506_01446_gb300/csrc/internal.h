@@ -55,6 +55,7 @@ struct Options {
     int use_graph = 1;
     int keys_per_thread_log2 = 0;
     int io_direct = 0;
+    int l2_prefetch = 1;
     int pipeline = 0;
 };
 

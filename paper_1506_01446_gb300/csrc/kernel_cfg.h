@@ -38,13 +38,16 @@ const TileCfg& tile_cfg(int id);
 // store (descending 4-byte sorts run ascending on ~key).
 cudaError_t launch_tile(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
                         const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
-                        cudaStream_t s);
+                        cudaStream_t s, uint32_t pf_dist = 0);
 cudaError_t launch_tile_u32(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
                             const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
-                            cudaStream_t s);
+                            uint32_t pf_dist, cudaStream_t s);
 cudaError_t launch_tile_u64(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
                             const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
-                            cudaStream_t s);
+                            uint32_t pf_dist, cudaStream_t s);
+cudaError_t tile_blocks_per_sm_u32(int cfg, int* blocks);
+cudaError_t tile_blocks_per_sm_u64(int cfg, int* blocks);
+cudaError_t tile_blocks_per_sm(int cfg, int* blocks);
 cudaError_t init_tile_attributes_u32();
 cudaError_t init_tile_attributes_u64();
 cudaError_t launch_pipe(int mode, int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,

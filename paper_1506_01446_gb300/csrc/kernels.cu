@@ -74,11 +74,17 @@ cudaError_t launch_step_t(K* base, uint32_t lo, uint32_t hi, uint32_t N, int j, 
 
 cudaError_t launch_tile(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
                         const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
-                        cudaStream_t s)
+                        cudaStream_t s, uint32_t pf_dist)
 {
     if (tile_cfg(cfg).key_bytes == 4)
-        return launch_tile_u32(cfg, base, lo, hi, hP, dP, grid, complement_in, complement_out, s);
-    return launch_tile_u64(cfg, base, lo, hi, hP, dP, grid, 0, 0, s);
+        return launch_tile_u32(cfg, base, lo, hi, hP, dP, grid, complement_in, complement_out, pf_dist, s);
+    return launch_tile_u64(cfg, base, lo, hi, hP, dP, grid, 0, 0, pf_dist, s);
+}
+
+// Resident CTAs per SM of a tile configuration (after init_tile_attributes).
+cudaError_t tile_blocks_per_sm(int cfg, int* blocks)
+{
+    return tile_cfg(cfg).key_bytes == 4 ? tile_blocks_per_sm_u32(cfg, blocks) : tile_blocks_per_sm_u64(cfg, blocks);
 }
 
 // Raises the dynamic shared-memory limit of every tile kernel on the current

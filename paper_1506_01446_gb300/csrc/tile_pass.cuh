@@ -7,6 +7,7 @@
 
 #include "engine.cuh"
 #include "patterns.h"
+#include "tma.cuh"
 
 namespace bitonic {
 
@@ -91,9 +92,34 @@ __device__ __forceinline__ void run_tile_rounds(Tile<K, DESC, LOG_R, LOG_T>& t,
 
 // One tile pass (Sections 4.1 and 4.2): load a tile of 2^m keys, run the
 // rounds (register network steps, shared-memory transposes in between), store.
+// Prefetches into L2 the rows of the tile `dist` CTAs ahead (the one a CTA
+// starting about one resident wave later will load), with TMA bulk
+// prefetches: no registers or shared memory are spent on it.
+template <typename K, int LOG_T, class PT>
+__device__ __forceinline__ void prefetch_tile_l2(const K* base, uint32_t lo, uint32_t hi, const PT& P, uint32_t dist)
+{
+    const uint32_t t = blockIdx.x + dist;
+    if (!dist || t >= gridDim.x) return;
+    const uint32_t g0 = cta_base(P, t);
+    const int c = P.row_log;
+    const uint32_t row_len = 1u << c;
+    const uint32_t nrows = 1u << (P.m - c);
+    // rows longer than 32 KiB are prefetched in 32 KiB pieces
+    const uint32_t piece = row_len > 8192u ? 8192u : row_len;
+    const uint32_t pieces = row_len / piece;
+    for (uint32_t i = threadIdx.x; i < nrows * pieces; i += (1u << LOG_T)) {
+        const uint32_t r = i / pieces, q = i % pieces;
+        uint32_t g = g0;
+        for (int j = 0; j < P.m - c; ++j)
+            if ((r >> j) & 1u) g ^= P.gvec[c + j];
+        g += q * piece;
+        if (g >= lo && g + piece <= hi) l2_prefetch_bulk(base + g, piece * (uint32_t)sizeof(K));
+    }
+}
+
 template <typename K, bool DESC, int LOG_R, int LOG_T, bool CATALOG, class PT>
 __device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uint32_t hi, const PT& P, K cm_in,
-                                          K cm_out)
+                                          K cm_out, uint32_t pf_dist = 0)
 {
     using T = Tile<K, DESC, LOG_R, LOG_T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -107,6 +133,7 @@ __device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uin
         t.load_global_interior(base, P.io[0], g0, x, cm_in);
     else
         t.load_global(base, lo, hi, P.io[0], g0, x, cm_in);
+    prefetch_tile_l2<K, LOG_T>(base, lo, hi, P, pf_dist);
     run_tile_rounds<K, DESC, LOG_R, LOG_T, CATALOG>(t, sm, P, x);
     if (interior)
         t.store_global_interior(base, P.io[1], g0, x, cm_out);
@@ -119,9 +146,10 @@ __device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uin
 // ones (a descending sort runs as an ascending sort of ~key).
 template <typename K, int LOG_R, int LOG_T>
 __global__ void __launch_bounds__(1 << LOG_T)
-k_tile(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P, K cm_in, K cm_out)
+k_tile(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P, K cm_in, K cm_out,
+       uint32_t pf_dist)
 {
-    tile_pass<K, false, LOG_R, LOG_T, true>(base, lo, hi, P, cm_in, cm_out);
+    tile_pass<K, false, LOG_R, LOG_T, true>(base, lo, hi, P, cm_in, cm_out, pf_dist);
 }
 
 // Descriptor with more rounds than fit by value, read from global memory.
@@ -135,16 +163,23 @@ k_tile_big(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParamsBig* 
 // Launcher and attribute setup of one configuration.
 template <typename K, int LR, int LT>
 cudaError_t launch_tile_t(void* base, uint32_t lo, uint32_t hi, const TileParams* hP, const TileParamsBig* dP,
-                          uint32_t grid, int complement_in, int complement_out, cudaStream_t s)
+                          uint32_t grid, int complement_in, int complement_out, uint32_t pf_dist, cudaStream_t s)
 {
     constexpr int kThreads = 1 << LT;
     constexpr size_t kSmem = (size_t(1) << (LR + LT)) * sizeof(K);
     const K ci = complement_in ? ~K(0) : K(0), co = complement_out ? ~K(0) : K(0);
     if (hP)
-        k_tile<K, LR, LT><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, *hP, ci, co);
+        k_tile<K, LR, LT><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, *hP, ci, co, pf_dist);
     else
         k_tile_big<K, LR, LT><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, dP, ci, co);
     return cudaGetLastError();
+}
+
+template <typename K, int LR, int LT>
+cudaError_t tile_occupancy_t(int* blocks)
+{
+    constexpr int kSmem = (int)((size_t(1) << (LR + LT)) * sizeof(K));
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_tile<K, LR, LT>, 1 << LT, kSmem);
 }
 
 template <typename K, int LR, int LT>

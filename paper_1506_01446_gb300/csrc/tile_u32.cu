@@ -6,10 +6,10 @@ namespace bitonic {
 
 cudaError_t launch_tile_u32(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
                             const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
-                            cudaStream_t s)
+                            uint32_t pf_dist, cudaStream_t s)
 {
 #define BITONIC_CASE(ID, KT, LR, LT) \
-    case ID: return launch_tile_t<KT, LR, LT>(base, lo, hi, hP, dP, grid, complement_in, complement_out, s);
+    case ID: return launch_tile_t<KT, LR, LT>(base, lo, hi, hP, dP, grid, complement_in, complement_out, pf_dist, s);
     switch (cfg) {
         BITONIC_TILE_CONFIGS_U32(BITONIC_CASE)
         default: return cudaErrorInvalidValue;
@@ -25,6 +25,17 @@ cudaError_t init_tile_attributes_u32()
     BITONIC_TILE_CONFIGS_U32(BITONIC_ATTR)
 #undef BITONIC_ATTR
     return e;
+}
+
+cudaError_t tile_blocks_per_sm_u32(int cfg, int* blocks)
+{
+#define BITONIC_OCC(ID, KT, LR, LT) \
+    case ID: return tile_occupancy_t<KT, LR, LT>(blocks);
+    switch (cfg) {
+        BITONIC_TILE_CONFIGS_U32(BITONIC_OCC)
+        default: return cudaErrorInvalidValue;
+    }
+#undef BITONIC_OCC
 }
 
 }  // namespace bitonic

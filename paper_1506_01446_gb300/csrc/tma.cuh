@@ -77,4 +77,11 @@ __device__ __forceinline__ void tma_load_bulk(void* dst, const void* src, uint32
         : "memory");
 }
 
+// Asks the TMA unit to bring `bytes` (multiple of 16, 16-byte aligned) of
+// global memory into L2 without waiting for it.
+__device__ __forceinline__ void l2_prefetch_bulk(const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 }  // namespace bitonic
