@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop leg")
     ap.add_argument("--serving-requests", type=int, default=20000)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--no-pairs", action="store_true", help="skip the key/value leg")
+    ap.add_argument("--ablation", action="store_true",
+                    help="also time the paper's three GPU variants (Basic / Semi / Optimized) over its sizes")
     return ap.parse_args()
 
 
@@ -125,6 +128,64 @@ def segmented_leg(bt, torch, steps):
     return {"arrays": 65536, "keys": nkeys, "batched_ms": batched_ms, "batched_gkeys_s": nkeys / batched_ms / 1e6,
             "per_array_ms": per_array_ms, "speedup": per_array_ms / batched_ms, "sampled_sorted": bool(ok),
             "note": "per-array form = 65,536 bitonic_sort_u32 calls (plain launches) on one stream"}
+
+
+def pairs_leg(bt, torch, steps):
+    """2^26 key/value pairs, keys uniform over [0, 2^20) (many ties), values =
+    original index, ascending, ties by index."""
+    n = 1 << 26
+    k_np, v_np = workloads.pair_keys_u32(n, seed=workloads.SEEDS["pairs_n26"])
+    ks, vs = torch.from_numpy(k_np.view(np.int32)).cuda(), torch.from_numpy(v_np.view(np.int32)).cuda()
+    kb, vb = ks.clone(), vs.clone()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        kb.copy_(ks)
+        vb.copy_(vs)
+        bt.sort_pairs_(kb, vb)
+    times = []
+    for _ in range(steps):
+        kb.copy_(ks)
+        vb.copy_(vs)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bt.sort_pairs_(kb, vb)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    ms = statistics.median(times)
+    out_k = kb[:: 1 << 10].cpu().numpy().view(np.uint32)
+    info = bt.plan_info(n, pairs=True)
+    return {"n": n, "ms": ms, "gpairs_s": n / ms / 1e6, "plan": info, "sampled_sorted": bool(np.all(out_k[1:] >= out_k[:-1]))}
+
+
+def ablation_leg(bt, torch):
+    """Section 5, Table 1 in shape: the Basic (one kernel per step, Section 3.3),
+    Semi (shared memory, Section 4.1) and Optimized (registers too, Section 4.2)
+    variants over the paper's sizes 2^17..2^28."""
+    saved = bt.get_options()
+    rows = []
+    for k in range(17, 29):
+        n = 1 << k
+        src = torch.randint(-2**31, 2**31 - 1, (n,), dtype=torch.int32, device="cuda")
+        buf = src.clone()
+        row = {"n_log2": k}
+        for name, var in (("basic", 1), ("semi", 2), ("optimized", 0)):
+            bt.set_options(variant=var)
+            buf.copy_(src)
+            bt.sort_(buf)
+            ts = []
+            for _ in range(3):
+                buf.copy_(src)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                bt.sort_(buf)
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            row[name + "_ms"] = min(ts)
+        rows.append(row)
+    bt.set_options(**saved)
+    return rows
 
 
 def serving_leg(bt, requests):
@@ -383,6 +444,10 @@ def main():
                        "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms}
         out = host_out.numpy().view(np.uint32)
         assert np.all(out[1:] >= out[:-1])
+    if not args.no_pairs and rank == 0:
+        line["pairs"] = pairs_leg(bt, torch, max(3, args.steps))
+    if args.ablation and rank == 0:
+        line["ablation"] = ablation_leg(bt, torch)
     if not args.no_segmented and rank == 0:
         line["segmented"] = segmented_leg(bt, torch, max(3, args.steps))
     if not args.no_serving and rank == 0:
