@@ -263,6 +263,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def reduce_max(x: float, world: int) -> float:
+    """Maximum of x over all ranks (the slowest rank sets the job's time)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank sorts its own array (replicas, no exchange between ranks)."""
+    return workloads.SEEDS["n28_uniform"] + rank
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -333,7 +350,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = 1 << args.n_log2
     hbm_gbs, peak_src = load_peaks()
-    keys_np = workloads.uniform_u32(n, seed=workloads.SEEDS["n28_uniform"] + rank)
+    keys_np = workloads.uniform_u32(n, seed=replica_seed(rank))
     tuned = None
     if not args.no_tune:
         import tempfile
@@ -370,11 +387,7 @@ def main():
             ends[i].record(stream)
         barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(sum(step_ms), world)
     ms_per_step = total_ms / args.steps
     value = n * world * args.steps / (total_ms / 1e3) / 1e9
 
