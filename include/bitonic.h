@@ -154,6 +154,12 @@ typedef struct {
     int io_direct;        /* bit 0: load a tile straight into its first round's register layout,
                              bit 1: store straight from its last round's layout (instead of an
                              extra shared-memory transpose into a coalesced layout); 0 = off */
+    int ctas_per_sm;      /* tile kernels: 3 = registers capped for three resident CTAs per SM
+                             where such a kernel exists for the tile shape, else uncapped;
+                             2 = uncapped (two CTAs); 0 = automatic (3 for 4-byte keys, 2 for
+                             pairs; default) */
+    int min_row_log2;     /* shortest run of consecutive keys a multi-stride pass moves, log2
+                             (keys); 0 = 128 bytes.  Shorter rows fit one more stride per pass. */
     int l2_prefetch;      /* > 0: each tile CTA asks the TMA unit to prefetch into L2 the tile
                              that many resident waves ahead (default 1); 0 = off */
     int pipeline;         /* 0 = one CTA per tile (default); persistent CTAs that prefetch the

@@ -4,7 +4,9 @@ the fastest.
 A candidate is a tile size (tile_log2), keys held per thread in registers
 (keys_per_thread_log2), the fused-stride cutoff (global_bits: the most
 strides at or above the tile size one pass may take; 0 = as many as fit) and
-the L2 prefetch distance (l2_prefetch, in resident waves).
+the L2 prefetch distance (l2_prefetch, in resident waves) and the register
+cap (ctas_per_sm: 3 = kernels capped for three resident CTAs per SM, 2 =
+uncapped).
 For every size class 2^k the tuner times each candidate with CUDA events on
 data already in device memory, picks the fastest, installs it with
 bitonic_set_class_options and caches the choices as JSON per GPU name (path:
@@ -20,15 +22,17 @@ import statistics
 from . import set_class_options, sort_, sort_pairs_
 
 CANDIDATES_U32 = (
-    dict(tile_log2=14, keys_per_thread_log2=6, global_bits=0, l2_prefetch=1),
-    dict(tile_log2=14, keys_per_thread_log2=6, global_bits=8, l2_prefetch=1),
-    dict(tile_log2=14, keys_per_thread_log2=6, global_bits=8, l2_prefetch=0),
-    dict(tile_log2=13, keys_per_thread_log2=5, global_bits=0, l2_prefetch=1),
+    dict(tile_log2=14, keys_per_thread_log2=6, global_bits=8, l2_prefetch=1, ctas_per_sm=3),
+    dict(tile_log2=14, keys_per_thread_log2=6, global_bits=0, l2_prefetch=1, ctas_per_sm=3),
+    dict(tile_log2=14, keys_per_thread_log2=6, global_bits=8, l2_prefetch=1, ctas_per_sm=2),
+    dict(tile_log2=14, keys_per_thread_log2=6, global_bits=8, l2_prefetch=0, ctas_per_sm=3),
+    dict(tile_log2=13, keys_per_thread_log2=5, global_bits=0, l2_prefetch=1, ctas_per_sm=2),
 )
 CANDIDATES_PAIRS = (
-    dict(tile_log2=13, keys_per_thread_log2=5, global_bits=0, l2_prefetch=1),
-    dict(tile_log2=13, keys_per_thread_log2=5, global_bits=7, l2_prefetch=1),
-    dict(tile_log2=12, keys_per_thread_log2=4, global_bits=0, l2_prefetch=1),
+    dict(tile_log2=13, keys_per_thread_log2=5, global_bits=0, l2_prefetch=1, ctas_per_sm=3),
+    dict(tile_log2=13, keys_per_thread_log2=5, global_bits=0, l2_prefetch=1, ctas_per_sm=2),
+    dict(tile_log2=13, keys_per_thread_log2=5, global_bits=7, l2_prefetch=1, ctas_per_sm=3),
+    dict(tile_log2=12, keys_per_thread_log2=4, global_bits=0, l2_prefetch=1, ctas_per_sm=2),
 )
 
 
@@ -106,7 +110,8 @@ def install(choices: dict) -> int:
     count = 0
     for kind, kb in (("uint32", 4), ("pairs", 8)):
         for k, c in choices.get(kind, {}).items():
-            opts = {f: c[f] for f in ("tile_log2", "keys_per_thread_log2", "global_bits", "l2_prefetch") if f in c}
+            opts = {f: c[f] for f in ("tile_log2", "keys_per_thread_log2", "global_bits", "l2_prefetch",
+                                      "min_row_log2", "ctas_per_sm") if f in c}
             set_class_options(kb, int(k), opts)
             count += 1
     return count

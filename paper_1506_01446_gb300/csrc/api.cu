@@ -65,18 +65,24 @@ Options resolve_options(int key_bytes, int k)
     o.global_bits = it->second.global_bits;
     o.pipeline = it->second.pipeline;
     o.l2_prefetch = it->second.l2_prefetch;
+    o.min_row_log2 = it->second.min_row_log2;
+    o.ctas_per_sm = it->second.ctas_per_sm;
     return o;
 }
 
-int options_code(const Options& o)
+// Packs every option that changes a plan into one key (5 bits per field).
+uint64_t options_code(const Options& o)
 {
-    return ((((o.variant * 16 + o.tile_log2) * 16 + o.keys_per_thread_log2) * 32 + o.global_bits) * 4 +
-            o.io_direct) * 64 + o.pipeline * 16 + o.l2_prefetch;
+    const int f[] = {o.variant, o.tile_log2, o.keys_per_thread_log2, o.global_bits, o.io_direct,
+                     o.pipeline, o.l2_prefetch, o.min_row_log2, o.ctas_per_sm};
+    uint64_t c = 0;
+    for (int v : f) c = (c << 5) | uint64_t(v & 31);
+    return c;
 }
 
-using PlanKey = std::tuple<uint64_t, int, int>;  // N, key bytes, options_code
-// op, n, ascending, ptr a, ptr b, ptr c, count, stream, variant, tile, gbits
-using GraphKey = std::tuple<int, uint64_t, int, uintptr_t, uintptr_t, uintptr_t, int, uintptr_t, int, int, int>;
+using PlanKey = std::tuple<uint64_t, int, uint64_t>;  // N, key bytes, options_code
+// op, n, ascending, ptr a, ptr b, ptr c, count, stream, options_code, unused
+using GraphKey = std::tuple<int, uint64_t, int, uintptr_t, uintptr_t, uintptr_t, int, uintptr_t, int, uint64_t, int>;
 
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
@@ -569,6 +575,8 @@ bitonic_status bitonic_set_options(const bitonic_options* opt)
     g_opt.pipeline = (opt->pipeline >= 0 && opt->pipeline <= 2) ? opt->pipeline : 0;
     g_opt.io_direct = opt->io_direct & 3;
     g_opt.l2_prefetch = opt->l2_prefetch < 0 ? 0 : (opt->l2_prefetch > 8 ? 8 : opt->l2_prefetch);
+    g_opt.min_row_log2 = (opt->min_row_log2 < 0 || opt->min_row_log2 > 12) ? 0 : opt->min_row_log2;
+    g_opt.ctas_per_sm = (opt->ctas_per_sm == 2 || opt->ctas_per_sm == 3) ? opt->ctas_per_sm : 0;
     return BITONIC_OK;
 }
 
@@ -591,12 +599,16 @@ bitonic_status bitonic_set_class_options(int key_bytes, int log2_n, const bitoni
     o.global_bits = opt->global_bits;
     o.pipeline = opt->pipeline;
     o.l2_prefetch = opt->l2_prefetch < 0 ? 0 : (opt->l2_prefetch > 8 ? 8 : opt->l2_prefetch);
+    o.min_row_log2 = (opt->min_row_log2 < 0 || opt->min_row_log2 > 12) ? 0 : opt->min_row_log2;
+    o.ctas_per_sm = (opt->ctas_per_sm == 2 || opt->ctas_per_sm == 3) ? opt->ctas_per_sm : 0;
     // the planner must accept the choice for this class
     Options probe = g_opt;
     probe.variant = 0;
     probe.tile_log2 = o.tile_log2;
     probe.keys_per_thread_log2 = o.keys_per_thread_log2;
     probe.global_bits = o.global_bits;
+    probe.min_row_log2 = o.min_row_log2;
+    probe.ctas_per_sm = o.ctas_per_sm;
     if (!make_plan(uint64_t(1) << log2_n, key_bytes, probe).ok) return BITONIC_ERR_UNSUPPORTED;
     g_class_opt[{key_bytes, log2_n}] = o;
     return BITONIC_OK;
@@ -614,6 +626,8 @@ bitonic_status bitonic_get_options(bitonic_options* opt)
     opt->pipeline = g_opt.pipeline;
     opt->io_direct = g_opt.io_direct;
     opt->l2_prefetch = g_opt.l2_prefetch;
+    opt->min_row_log2 = g_opt.min_row_log2;
+    opt->ctas_per_sm = g_opt.ctas_per_sm;
     return BITONIC_OK;
 }
 

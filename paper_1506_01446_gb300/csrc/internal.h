@@ -56,6 +56,8 @@ struct Options {
     int keys_per_thread_log2 = 0;
     int io_direct = 0;
     int l2_prefetch = 1;
+    int min_row_log2 = 0;
+    int ctas_per_sm = 0;
     int pipeline = 0;
 };
 

@@ -8,16 +8,20 @@
 
 #include "desc.h"
 
-#define BITONIC_TILE_CONFIGS_U32(X)                                      \
-    X(0, uint32_t, 6, 8)  /* 16K keys, 256 threads x 64 keys */         \
-    X(1, uint32_t, 5, 8)  /*  8K keys, 256 threads x 32 keys */         \
-    X(2, uint32_t, 5, 9)  /* 16K keys, 512 threads x 32 keys */         \
-    X(3, uint32_t, 3, 10) /*  8K keys, 1024 threads x 8 keys (semi) */
+// (id, key type, log2 keys per thread, log2 threads, resident CTAs per SM
+// the registers are capped for: 1 = no cap)
+#define BITONIC_TILE_CONFIGS_U32(X)                                          \
+    X(0, uint32_t, 6, 8, 1)  /* 16K keys, 256 threads x 64 keys */          \
+    X(1, uint32_t, 5, 8, 1)  /*  8K keys, 256 threads x 32 keys */          \
+    X(2, uint32_t, 5, 9, 1)  /* 16K keys, 512 threads x 32 keys */          \
+    X(3, uint32_t, 3, 10, 1) /*  8K keys, 1024 threads x 8 keys (semi) */   \
+    X(7, uint32_t, 6, 8, 3)  /* 16K keys, 256 x 64, capped for 3 CTAs/SM */
 
-#define BITONIC_TILE_CONFIGS_U64(X)                                      \
-    X(4, uint64_t, 5, 8)  /*  8K composites, 256 threads x 32 */        \
-    X(5, uint64_t, 4, 8)  /*  4K composites, 256 threads x 16 */        \
-    X(6, uint64_t, 2, 10) /*  4K composites, 1024 threads x 4 (semi) */
+#define BITONIC_TILE_CONFIGS_U64(X)                                          \
+    X(4, uint64_t, 5, 8, 1)  /*  8K composites, 256 threads x 32 */         \
+    X(5, uint64_t, 4, 8, 1)  /*  4K composites, 256 threads x 16 */         \
+    X(6, uint64_t, 2, 10, 1) /*  4K composites, 1024 threads x 4 (semi) */  \
+    X(8, uint64_t, 5, 8, 3)  /*  8K composites, capped for 3 CTAs/SM */
 
 #define BITONIC_TILE_CONFIGS(X) BITONIC_TILE_CONFIGS_U32(X) BITONIC_TILE_CONFIGS_U64(X)
 
@@ -28,9 +32,10 @@ struct TileCfg {
     int key_bytes;
     int log_r;
     int log_t;
+    int min_blocks;
 };
 
-constexpr int kNumTileCfgs = 7;
+constexpr int kNumTileCfgs = 9;
 
 const TileCfg& tile_cfg(int id);
 

@@ -215,9 +215,9 @@ cudaError_t pipe_attr_t(int* blocks_per_sm)
 // Configurations compiled in pipelined form (the others report zero CTAs
 // per SM and run one CTA per tile).
 #define BITONIC_PIPE_CONFIGS(X) \
-    X(0, uint32_t, 6, 8)        \
-    X(1, uint32_t, 5, 8)        \
-    X(4, uint64_t, 5, 8)
+    X(0, uint32_t, 6, 8, 1)     \
+    X(1, uint32_t, 5, 8, 1)     \
+    X(4, uint64_t, 5, 8, 1)
 
 }  // namespace
 
@@ -225,7 +225,7 @@ cudaError_t launch_pipe(int mode, int cfg, void* base, uint32_t lo, uint32_t hi,
                         const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, int complement_in,
                         int complement_out, int* status, cudaStream_t s)
 {
-#define BITONIC_PIPE_CASE(ID, KT, LR, LT)                                                                   \
+#define BITONIC_PIPE_CASE(ID, KT, LR, LT, MB)                                                                 \
     case ID:                                                                                                \
         return launch_pipe_t<KT, LR, LT>(mode, base, lo, hi, hP, dP, ntiles, grid, complement_in, complement_out, \
                                          status, s);
@@ -243,7 +243,7 @@ cudaError_t init_pipe_attributes(int* blocks_per_sm)
 {
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < kNumTileCfgs; ++i) blocks_per_sm[i] = 0;
-#define BITONIC_PIPE_ATTR(ID, KT, LR, LT) \
+#define BITONIC_PIPE_ATTR(ID, KT, LR, LT, MB) \
     if (e == cudaSuccess) e = pipe_attr_t<KT, LR, LT>(&blocks_per_sm[ID]);
     BITONIC_PIPE_CONFIGS(BITONIC_PIPE_ATTR)
 #undef BITONIC_PIPE_ATTR

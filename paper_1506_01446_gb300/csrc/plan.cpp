@@ -15,11 +15,17 @@ namespace bitonic {
 
 namespace {
 
-const TileCfg kCfgs[kNumTileCfgs] = {
-#define BITONIC_CFG_ROW(ID, KT, LR, LT) {ID, (int)sizeof(KT), LR, LT},
+constexpr TileCfg cfg_row(int id)
+{
+#define BITONIC_CFG_ROW(ID, KT, LR, LT, MB) \
+    if (id == ID) return TileCfg{ID, (int)sizeof(KT), LR, LT, MB};
     BITONIC_TILE_CONFIGS(BITONIC_CFG_ROW)
 #undef BITONIC_CFG_ROW
-};
+    return TileCfg{-1, 0, 0, 0, 0};
+}
+
+const TileCfg kCfgs[kNumTileCfgs] = {cfg_row(0), cfg_row(1), cfg_row(2), cfg_row(3), cfg_row(4),
+                                     cfg_row(5), cfg_row(6), cfg_row(7), cfg_row(8)};
 
 struct LStep {
     int bit;
@@ -161,7 +167,8 @@ bool emit_round(const HostRound& hr, int log_t, int m, int vb, RoundDesc& rd)
 // each quarter warp then touches one aligned 128-byte line.
 bool round_coalesced(const RoundDesc& rd, const TileParamsBig& P, int vb)
 {
-    for (int t = 0; t < 3; ++t) {
+    const int need = std::min(3, (int)P.row_log - vb);  // lanes that stay inside one row
+    for (int t = 0; t < need; ++t) {
         const int b = vb + t;
         if (rd.thr_loc[t] != (1u << b)) return false;
         if (P.gvec[b] != (1u << b)) return false;
@@ -291,19 +298,29 @@ int choose_cfg(int key_bytes, const Options& opt)
     // Default keys per thread: 64 for 4-byte keys, 32 for composites, else
     // the largest configured value below that.
     const int pref_r = opt.keys_per_thread_log2 ? opt.keys_per_thread_log2 : (key_bytes == 4 ? 6 : 5);
-    int best = -1;
-    for (int i = 0; i < kNumTileCfgs; ++i) {
-        const TileCfg& c = kCfgs[i];
-        if (c.key_bytes != key_bytes) continue;
-        const bool c_semi = c.log_r == vb + 1;
-        if (semi != c_semi) continue;
-        if (semi) return i;
-        if (c.log_r + c.log_t != tile) continue;
-        if (opt.keys_per_thread_log2 && c.log_r != opt.keys_per_thread_log2) continue;
-        if (c.log_r > pref_r) continue;
-        if (best < 0 || c.log_r > kCfgs[best].log_r) best = i;
+    // Register cap: 3 = kernels capped for three resident CTAs per SM, 2 =
+    // uncapped, 0 = capped for 4-byte keys only (the capped composite kernel
+    // spills and loses).  A cap is taken where a capped kernel of this shape
+    // exists; other shapes fall back to the uncapped kernel.
+    const int cap = opt.ctas_per_sm ? opt.ctas_per_sm : (key_bytes == 4 ? 3 : 2);
+    const int want_blocks = cap == 3 ? 3 : 1;
+    for (int blocks : {want_blocks, 1}) {
+        int best = -1;
+        for (int i = 0; i < kNumTileCfgs; ++i) {
+            const TileCfg& c = kCfgs[i];
+            if (c.key_bytes != key_bytes) continue;
+            const bool c_semi = c.log_r == vb + 1;
+            if (semi != c_semi) continue;
+            if (semi) return i;
+            if (c.log_r + c.log_t != tile) continue;
+            if (opt.keys_per_thread_log2 && c.log_r != opt.keys_per_thread_log2) continue;
+            if (c.log_r > pref_r) continue;
+            if (c.min_blocks != blocks) continue;
+            if (best < 0 || c.log_r > kCfgs[best].log_r) best = i;
+        }
+        if (best >= 0) return best;
     }
-    return best;
+    return -1;
 }
 
 struct GStep {
@@ -331,7 +348,7 @@ const TileCfg& tile_cfg(int id) { return kCfgs[id]; }
 bool make_class_desc(int key_bytes, int k, TileParamsBig& P)
 {
     std::memset(&P, 0, sizeof(P));
-    const int cfg_id = key_bytes == 4 ? 0 : 4;
+    const int cfg_id = key_bytes == 4 ? 0 : 4;  // the packed segmented kernels use these two
     const TileCfg& cfg = kCfgs[cfg_id];
     const int vb = key_bytes == 4 ? 2 : 1;
     const int m = cfg.log_r + cfg.log_t;
@@ -365,7 +382,8 @@ Plan make_plan(uint64_t nv, int key_bytes, const Options& opt)
     const TileCfg& cfg = kCfgs[cfg_id];
     const int vb = key_bytes == 4 ? 2 : 1;
     const int m = cfg.log_r + cfg.log_t;
-    const int c_min = vb + 3;  // rows of at least 128 bytes
+    // rows of at least 128 bytes by default (one line per quarter warp)
+    const int c_min = opt.min_row_log2 ? std::max(vb + 1, opt.min_row_log2) : vb + 3;
     const bool semi = opt.variant == 2;
     const bool fuse = !semi;   // let a pass run across a phase boundary
     int high_limit = semi ? 1 : (opt.global_bits > 0 ? opt.global_bits : 64);

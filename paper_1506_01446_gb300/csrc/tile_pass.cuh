@@ -144,8 +144,8 @@ __device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uin
 // Descriptor passed by value: every thread reads it through the constant
 // bank.  Keys are complemented on load / store when cm_in / cm_out are all
 // ones (a descending sort runs as an ascending sort of ~key).
-template <typename K, int LOG_R, int LOG_T>
-__global__ void __launch_bounds__(1 << LOG_T)
+template <typename K, int LOG_R, int LOG_T, int MINB>
+__global__ void __launch_bounds__(1 << LOG_T, MINB)
 k_tile(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P, K cm_in, K cm_out,
        uint32_t pf_dist)
 {
@@ -153,15 +153,15 @@ k_tile(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ T
 }
 
 // Descriptor with more rounds than fit by value, read from global memory.
-template <typename K, int LOG_R, int LOG_T>
-__global__ void __launch_bounds__(1 << LOG_T)
+template <typename K, int LOG_R, int LOG_T, int MINB>
+__global__ void __launch_bounds__(1 << LOG_T, MINB)
 k_tile_big(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParamsBig* __restrict__ P, K cm_in, K cm_out)
 {
     tile_pass<K, false, LOG_R, LOG_T, false>(base, lo, hi, *P, cm_in, cm_out);
 }
 
 // Launcher and attribute setup of one configuration.
-template <typename K, int LR, int LT>
+template <typename K, int LR, int LT, int MB>
 cudaError_t launch_tile_t(void* base, uint32_t lo, uint32_t hi, const TileParams* hP, const TileParamsBig* dP,
                           uint32_t grid, int complement_in, int complement_out, uint32_t pf_dist, cudaStream_t s)
 {
@@ -169,30 +169,31 @@ cudaError_t launch_tile_t(void* base, uint32_t lo, uint32_t hi, const TileParams
     constexpr size_t kSmem = (size_t(1) << (LR + LT)) * sizeof(K);
     const K ci = complement_in ? ~K(0) : K(0), co = complement_out ? ~K(0) : K(0);
     if (hP)
-        k_tile<K, LR, LT><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, *hP, ci, co, pf_dist);
+        k_tile<K, LR, LT, MB><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, *hP, ci, co, pf_dist);
     else
-        k_tile_big<K, LR, LT><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, dP, ci, co);
+        k_tile_big<K, LR, LT, MB><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, dP, ci, co);
     return cudaGetLastError();
 }
 
-template <typename K, int LR, int LT>
+template <typename K, int LR, int LT, int MB>
 cudaError_t tile_occupancy_t(int* blocks)
 {
     constexpr int kSmem = (int)((size_t(1) << (LR + LT)) * sizeof(K));
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_tile<K, LR, LT>, 1 << LT, kSmem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_tile<K, LR, LT, MB>, 1 << LT, kSmem);
 }
 
-template <typename K, int LR, int LT>
+template <typename K, int LR, int LT, int MB>
 cudaError_t tile_attr_t()
 {
     constexpr int kSmem = (int)((size_t(1) << (LR + LT)) * sizeof(K));
-    cudaError_t e = cudaFuncSetAttribute(k_tile<K, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_tile<K, LR, LT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_tile_big<K, LR, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        e = cudaFuncSetAttribute(k_tile_big<K, LR, LT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     // Prefer the largest shared-memory carve-out so that every CTA the
     // registers allow can be resident.
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_tile<K, LR, LT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        e = cudaFuncSetAttribute(k_tile<K, LR, LT, MB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return e;
 }
 

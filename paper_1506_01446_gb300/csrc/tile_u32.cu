@@ -8,8 +8,8 @@ cudaError_t launch_tile_u32(int cfg, void* base, uint32_t lo, uint32_t hi, const
                             const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
                             uint32_t pf_dist, cudaStream_t s)
 {
-#define BITONIC_CASE(ID, KT, LR, LT) \
-    case ID: return launch_tile_t<KT, LR, LT>(base, lo, hi, hP, dP, grid, complement_in, complement_out, pf_dist, s);
+#define BITONIC_CASE(ID, KT, LR, LT, MB) \
+    case ID: return launch_tile_t<KT, LR, LT, MB>(base, lo, hi, hP, dP, grid, complement_in, complement_out, pf_dist, s);
     switch (cfg) {
         BITONIC_TILE_CONFIGS_U32(BITONIC_CASE)
         default: return cudaErrorInvalidValue;
@@ -20,8 +20,8 @@ cudaError_t launch_tile_u32(int cfg, void* base, uint32_t lo, uint32_t hi, const
 cudaError_t init_tile_attributes_u32()
 {
     cudaError_t e = cudaSuccess;
-#define BITONIC_ATTR(ID, KT, LR, LT) \
-    if (e == cudaSuccess) e = tile_attr_t<KT, LR, LT>();
+#define BITONIC_ATTR(ID, KT, LR, LT, MB) \
+    if (e == cudaSuccess) e = tile_attr_t<KT, LR, LT, MB>();
     BITONIC_TILE_CONFIGS_U32(BITONIC_ATTR)
 #undef BITONIC_ATTR
     return e;
@@ -29,8 +29,8 @@ cudaError_t init_tile_attributes_u32()
 
 cudaError_t tile_blocks_per_sm_u32(int cfg, int* blocks)
 {
-#define BITONIC_OCC(ID, KT, LR, LT) \
-    case ID: return tile_occupancy_t<KT, LR, LT>(blocks);
+#define BITONIC_OCC(ID, KT, LR, LT, MB) \
+    case ID: return tile_occupancy_t<KT, LR, LT, MB>(blocks);
     switch (cfg) {
         BITONIC_TILE_CONFIGS_U32(BITONIC_OCC)
         default: return cudaErrorInvalidValue;

@@ -29,10 +29,10 @@ def to_host(t) -> np.ndarray:
 @pytest.fixture(autouse=True)
 def default_options():
     bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1, keys_per_thread_log2=0, pipeline=0,
-                   l2_prefetch=1)
+                   l2_prefetch=1, min_row_log2=0, ctas_per_sm=0)
     yield
     bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1, keys_per_thread_log2=0, pipeline=0,
-                   l2_prefetch=1)
+                   l2_prefetch=1, min_row_log2=0, ctas_per_sm=0)
     assert bt.last_device_error() == bt.OK
 
 
@@ -92,10 +92,13 @@ def test_n24_non_power_of_two():
 
 
 @pytest.mark.parametrize("variant,tile,kpt,pipeline", [(1, 0, 0, 0), (2, 0, 0, 0), (0, 13, 0, 0), (0, 14, 5, 0),
-                                                      (0, 14, 6, 1), (0, 13, 5, 1), (0, 14, 6, 2), (0, 13, 5, 2)])
+                                                      (0, 14, 6, 1), (0, 13, 5, 1), (0, 14, 6, 2), (0, 13, 5, 2),
+                                                      (0, 14, 6, 3)])
 def test_variants_agree(variant, tile, kpt, pipeline):
-    bt.set_options(variant=variant, tile_log2=tile, keys_per_thread_log2=kpt, pipeline=pipeline,
-                   l2_prefetch=0 if variant == 0 and tile == 13 else 1)
+    uncapped = pipeline == 3  # (pipeline column 3: the uncapped two-CTA kernel, one CTA per tile)
+    bt.set_options(variant=variant, tile_log2=tile, keys_per_thread_log2=kpt, pipeline=0 if uncapped else pipeline,
+                   l2_prefetch=0 if variant == 0 and tile == 13 else 1, ctas_per_sm=2 if uncapped else 3,
+                   min_row_log2=3 if (kpt == 5 and pipeline == 0) else 0)
     for n in [3, 4097, 65537, 1 << 19]:
         check_keys(workloads.uniform_u32(n, seed=n), True)
         check_keys(workloads.uniform_u32(n, seed=n), False, 1)
@@ -153,8 +156,10 @@ def test_profiled_launch_sequence():
     assert all(x >= 0 for x in times)
 
 
-@pytest.mark.parametrize("ascending", [True, False])
-def test_pairs_small(ascending):
+@pytest.mark.parametrize("ascending,cap", [(True, 0), (False, 0), (True, 3)])
+def test_pairs_small(ascending, cap):
+    # cap 3: the composite tile kernel capped for three resident CTAs per SM
+    bt.set_options(ctas_per_sm=cap)
     for n in [2, 3, 100, 4097, 8193, 70001, 1 << 18]:
         keys = (workloads.uniform_u32(n, seed=n) >> np.uint32(26)).astype(np.uint32)  # many ties
         vals = workloads.uniform_u32(n, seed=n + 7)

@@ -16,9 +16,11 @@ pytestmark = pytest.mark.skipif(not __import__("os").path.exists(bt.LIB_PATH),
 
 @pytest.fixture(autouse=True)
 def default_options():
-    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1, keys_per_thread_log2=0)
+    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1, keys_per_thread_log2=0, min_row_log2=0,
+                   ctas_per_sm=0)
     yield
-    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1, keys_per_thread_log2=0)
+    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1, keys_per_thread_log2=0, min_row_log2=0,
+                   ctas_per_sm=0)
 
 
 SIZES = [2, 3, 17, 4095, 4096, 8193, 16384, 16385, 70001, 1 << 17]
@@ -69,6 +71,20 @@ def test_direct_io_layouts(io_direct):
         got, _, st = emulate(keys, False, 2)
         assert np.array_equal(got, oracle.merge_sort(keys, False))
     bt.set_options(io_direct=0)
+
+
+@pytest.mark.parametrize("row", [3, 4, 6])
+def test_min_row_lengths(row):
+    bt.set_options(min_row_log2=row)
+    for n in (70001, (1 << 19) + 3):
+        keys = workloads.uniform_u32(n, seed=row)
+        got, plan, st = emulate(keys, True, 1)
+        assert np.array_equal(got, oracle.merge_sort(keys))
+        assert st.conflicted_quarter_warps == 0
+    comp = np.arange(100003, dtype=np.uint64)[::-1].copy()
+    got, _, _ = emulate(comp, True, 0)
+    assert np.array_equal(got, np.sort(comp))
+    bt.set_options(min_row_log2=0)
 
 
 @pytest.mark.parametrize("gb", [1, 2, 3, 5, 9])
