@@ -40,12 +40,34 @@ __device__ __forceinline__ uint32_t swz(uint32_t lv)
     return lv ^ (f & 7u);
 }
 
+// Multipliers 1 and 2^32 - 1 for the multiply-add form of a 4-byte
+// compare-exchange.  Read from constant memory, so the compiler cannot turn
+// the multiply-adds back into integer-ALU adds.
+static __constant__ uint32_t c_ce_mul[2] = {1u, 0xFFFFFFFFu};
+
+// Of every three 4-byte compare-exchanges of a step, how many take the
+// larger key as a + b - min(a, b) with two multiply-adds (FMA pipe) instead
+// of a max (integer ALU).  A compare-exchange is otherwise two min/max on
+// the integer ALU while the FMA pipe idles.
+#ifndef BITONIC_CE_FMA_THIRDS
+#define BITONIC_CE_FMA_THIRDS 2
+#endif
+
 // Compare-exchange: the lower register receives the key that sorts first.
+// fma_hi: the multiply-add form (4-byte keys; exact modulo 2^32, since the
+// minimum is one of the two keys).  Constant once the caller's loop unrolls.
 template <bool DESC, typename K>
-__device__ __forceinline__ void cmpx(K& a, K& b)
+__device__ __forceinline__ void cmpx(K& a, K& b, bool fma_hi = false)
 {
-    K lo = a < b ? a : b;
-    K hi = a < b ? b : a;
+    K lo, hi;
+    if (sizeof(K) == 4 && fma_hi) {
+        lo = a < b ? a : b;
+        const K sum = a * c_ce_mul[0] + b;
+        hi = lo * c_ce_mul[1] + sum;
+    } else {
+        lo = a < b ? a : b;
+        hi = a < b ? b : a;
+    }
     a = DESC ? hi : lo;
     b = DESC ? lo : hi;
 }
@@ -59,7 +81,7 @@ __device__ __forceinline__ void net_step(K (&r)[R])
     for (int i = 0; i < R; ++i) {
         if (i & (1 << Q)) continue;
         const int j = FLIP ? (i ^ ((2 << Q) - 1)) : (i | (1 << Q));
-        cmpx<DESC>(r[i], r[j]);
+        cmpx<DESC>(r[i], r[j], ((i + Q) % 3) < BITONIC_CE_FMA_THIRDS);
     }
 }
 
