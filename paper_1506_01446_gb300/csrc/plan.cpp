@@ -323,6 +323,14 @@ int choose_cfg(int key_bytes, const Options& opt)
     return -1;
 }
 
+// Relative cost of one more pass (a full read and write of the keys) against
+// one more shared-memory transpose inside a pass, measured on GB300 at
+// 2^28 keys: about 0.30 ms against 0.075 ms.
+#ifndef BITONIC_PASS_WEIGHT
+#define BITONIC_PASS_WEIGHT 4
+#endif
+constexpr int kPassWeight = BITONIC_PASS_WEIGHT;
+
 struct GStep {
     int bit;
     bool flip;
@@ -415,23 +423,28 @@ Plan make_plan(uint64_t nv, int key_bytes, const Options& opt)
         plan.fused_steps += ksort * (ksort + 1) / 2;
     }
 
-    // The remaining steps, split greedily into passes: a pass takes steps
-    // while their bits (plus the 2^c_min-key rows) fit in the tile.  A
-    // phase's mirror step may open a pass or follow the previous phase's last
-    // steps, provided its bit is the highest in the tile.
+    // The remaining steps, split into passes.  A pass takes a run of steps
+    // whose bits (plus the 2^c_min-key rows) fit in the tile; a phase's
+    // mirror step may open a pass or follow the previous phase's last steps,
+    // provided its bit is the highest in the tile.  The optimized variant
+    // picks the split by a dynamic program over the step index with cost
+    // kPassWeight per pass plus one per shared-memory transpose (a pass that
+    // ends one step later may need a whole extra transpose); the semi variant
+    // takes as many steps per pass as fit.
     std::vector<GStep> gs;
     for (int p = ksort + 1; p <= k; ++p) {
         gs.push_back({p - 1, true, p});
         for (int b = p - 2; b >= 0; --b) gs.push_back({b, false, p});
     }
-    size_t i = 0;
-    while (i < gs.size()) {
+    const size_t ng = gs.size();
+    // Longest feasible pass from step i (every shorter run is feasible too).
+    auto frontier = [&](size_t i) -> size_t {
         std::vector<int> B;
         for (int b = 0; b < c_min; ++b) B.push_back(b);
         size_t j = i;
         int nhigh = 0;
         bool flipped = false, has_low = false, has_high = false;
-        while (j < gs.size()) {
+        while (j < ng) {
             const GStep& g = gs[j];
             const bool high = g.bit >= m;
             if (g.flip && (flipped || B.back() > g.bit)) break;
@@ -449,16 +462,72 @@ Plan make_plan(uint64_t nv, int key_bytes, const Options& opt)
             nhigh += high ? 1 : 0;
             ++j;
         }
-        if (j == i) return plan;
-        // Fill the tile with the lowest free bits (longer contiguous rows).
-        for (int b = 0; (int)B.size() < m; ++b)
-            if (!contains(B, b)) B.push_back(b);
-        std::sort(B.begin(), B.end());
+        return j;
+    };
+    // Tile bits, local steps and descriptor of the pass over steps [i, j).
+    struct PassSpec {
+        std::vector<int> B;
         std::vector<LStep> ls;
+        bool flipped = false;
+        TileParamsBig P;
+    };
+    auto build_pass = [&](size_t i, size_t j, PassSpec& ps) -> bool {
+        ps.B.clear();
+        ps.ls.clear();
+        ps.flipped = false;
+        for (int b = 0; b < c_min; ++b) ps.B.push_back(b);
+        for (size_t s = i; s < j; ++s) {
+            if (!contains(ps.B, gs[s].bit)) ps.B.push_back(gs[s].bit);
+            ps.flipped |= gs[s].flip;
+        }
+        // Fill the tile with the lowest free bits (longer contiguous rows).
+        for (int b = 0; (int)ps.B.size() < m; ++b)
+            if (!contains(ps.B, b)) ps.B.push_back(b);
+        std::sort(ps.B.begin(), ps.B.end());
+        for (size_t s = i; s < j; ++s) {
+            const int lb = (int)(std::find(ps.B.begin(), ps.B.end(), gs[s].bit) - ps.B.begin());
+            ps.ls.push_back({lb, gs[s].flip});
+        }
+        std::memset(&ps.P, 0, sizeof(ps.P));
+        if (!map_bits(ps.P, ps.B, ps.flipped, k)) return false;
+        return plan_rounds(ps.ls, cfg, vb, opt.io_direct, ps.P);
+    };
+    std::vector<size_t> cut;  // pass boundaries
+    if (semi) {
+        for (size_t i = 0; i < ng;) {
+            const size_t j = frontier(i);
+            if (j == i) return plan;
+            cut.push_back(i);
+            i = j;
+        }
+    } else {
+        constexpr int kInf = 1 << 30;
+        std::vector<int> cost(ng + 1, kInf);
+        std::vector<size_t> prev(ng + 1, 0);
+        cost[0] = 0;
+        PassSpec ps;
+        for (size_t i = 0; i < ng; ++i) {
+            if (cost[i] >= kInf) continue;
+            const size_t jmax = frontier(i);
+            for (size_t j = i + 1; j <= jmax; ++j) {
+                if (!build_pass(i, j, ps)) continue;
+                const int c = cost[i] + kPassWeight + (int)ps.P.nrounds - 1;
+                if (c < cost[j]) {
+                    cost[j] = c;
+                    prev[j] = i;
+                }
+            }
+        }
+        if (cost[ng] >= kInf) return plan;
+        for (size_t j = ng; j > 0; j = prev[j]) cut.push_back(prev[j]);
+        std::reverse(cut.begin(), cut.end());
+    }
+    for (size_t q = 0; q < cut.size(); ++q) {
+        const size_t i = cut[q], j = q + 1 < cut.size() ? cut[q + 1] : ng;
+        PassSpec ps;
+        if (!build_pass(i, j, ps)) return plan;
         int hi = -1, lo = 64;
         for (size_t s = i; s < j; ++s) {
-            const int lb = (int)(std::find(B.begin(), B.end(), gs[s].bit) - B.begin());
-            ls.push_back({lb, gs[s].flip});
             hi = std::max(hi, gs[s].bit);
             lo = std::min(lo, gs[s].bit);
             if (gs[s].bit >= m) plan.global_steps += 1;
@@ -466,10 +535,9 @@ Plan make_plan(uint64_t nv, int key_bytes, const Options& opt)
         }
         bool contiguous = true;
         for (int b = 0; b < m; ++b)
-            if (B[b] != b) contiguous = false;
+            if (ps.B[b] != b) contiguous = false;
         const int kind = contiguous ? KIND_TILE_MERGE : KIND_GLOBAL;
-        if (!add_pass(B, flipped, ls, kind, gs[i].phase, hi, lo, flipped)) return plan;
-        i = j;
+        if (!add_pass(ps.B, ps.flipped, ps.ls, kind, gs[i].phase, hi, lo, ps.flipped)) return plan;
     }
     plan.ok = true;
     return plan;

@@ -122,3 +122,18 @@ def test_plan_info_headline_size():
     info = bt.plan_info(1 << 28)
     assert info["hbm_passes"] == info["launches"]
     assert info["hbm_passes"] <= 40
+
+
+def test_split_weighs_transposes():
+    # The optimized plan splits the steps into passes by cost (one pass = a
+    # read and a write of every key; one transpose = a shared-memory round
+    # trip inside a pass).  At 2^28 4-byte keys the greedy longest-pass split
+    # needs 27 passes and 82 transposes; the weighted split trades one pass
+    # for twelve transposes.
+    from plan_emulator import debug_plan
+    bt.set_options(variant=0, global_bits=8)
+    P = debug_plan(1 << 28, 4)
+    transposes = sum(int(P["descs"][L[5]]["nrounds"]) - 1 for L in P["launches"])
+    assert len(P["launches"]) <= 28
+    assert 4 * len(P["launches"]) + transposes <= 4 * 27 + 82 - 8
+    assert transposes <= 70
