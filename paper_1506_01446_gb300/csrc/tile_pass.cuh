@@ -143,13 +143,17 @@ __device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uin
 
 // Descriptor passed by value: every thread reads it through the constant
 // bank.  Keys are complemented on load / store when cm_in / cm_out are all
-// ones (a descending sort runs as an ascending sort of ~key).
+// ones (a descending sort runs as an ascending sort of ~key).  The round
+// catalog (straight-line code per round shape) pays for its instruction
+// footprint with 4-byte keys (2^28: 13.5 vs 14.7 ms on GB300) but not with
+// 8-byte composites (2^26 pairs: 10.33 vs 10.22 ms), which use per-step
+// dispatch.
 template <typename K, int LOG_R, int LOG_T, int MINB>
 __global__ void __launch_bounds__(1 << LOG_T, MINB)
 k_tile(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P, K cm_in, K cm_out,
        uint32_t pf_dist)
 {
-    tile_pass<K, false, LOG_R, LOG_T, true>(base, lo, hi, P, cm_in, cm_out, pf_dist);
+    tile_pass<K, false, LOG_R, LOG_T, sizeof(K) == 4>(base, lo, hi, P, cm_in, cm_out, pf_dist);
 }
 
 // Descriptor with more rounds than fit by value, read from global memory.
