@@ -13,6 +13,8 @@ Functions and the passages they follow:
                         (Section 3.2 closed forms)
   bitonic_merge         Section 3.1 bitonic merge (half-cleaner steps)
   bitonic_sort_pairs    the same network on (key, original index)
+  bitonic_sort_typed    the same network on int32 / float32 / uint64 / int64 /
+                        float64 keys (floats: IEEE 754-2008 totalOrder)
   merge_sort[_pairs]    independent stable top-down merge sort
   quicksort             Section 5 / Table 1 CPU comparison (median-of-three)
   zero_one_failures     0-1 principle over all 2^m zero-one inputs
@@ -66,6 +68,8 @@ def load(mutant: int = 0, out_dir: str | None = None) -> ctypes.CDLL:
     lib.oracle_is_sorted_u32.restype = i32
     lib.oracle_same_multiset_u32.argtypes = [_P32, _P32, u64]
     lib.oracle_same_multiset_u32.restype = i32
+    lib.oracle_bitonic_sort_typed.argtypes = [ctypes.c_void_p, u64, i32, i32, ctypes.POINTER(Counts)]
+    lib.oracle_bitonic_sort_typed.restype = i32
     lib.oracle_mutant_id.argtypes = []
     lib.oracle_mutant_id.restype = i32
     _LIBS[key] = lib
@@ -95,6 +99,25 @@ def bitonic_sort(keys, ascending: bool = True, first_descending: bool = False, l
     c = Counts()
     _check(lib.oracle_bitonic_sort_u32(_ptr(a), a.size, int(ascending), int(first_descending),
                                        ctypes.byref(c)), "bitonic_sort")
+    return a, c
+
+
+# key types of oracle_bitonic_sort_typed
+KEY_TYPES = {np.dtype(np.int32): 1, np.dtype(np.float32): 2, np.dtype(np.uint64): 3,
+             np.dtype(np.int64): 4, np.dtype(np.float64): 5}
+
+
+def bitonic_sort_typed(keys, ascending: bool = True, lib=None):
+    """Section 3.1 network on int32 / float32 / uint64 / int64 / float64 keys,
+    each ordered by its own definition (floats: IEEE 754-2008 totalOrder).
+    Returns (sorted copy, Counts); bit patterns are preserved."""
+    lib = lib or load()
+    a = np.ascontiguousarray(np.asarray(keys)).copy()
+    if a.dtype not in KEY_TYPES:
+        raise TypeError(f"unsupported key type {a.dtype}")
+    c = Counts()
+    _check(lib.oracle_bitonic_sort_typed(a.ctypes.data, a.size, KEY_TYPES[a.dtype], int(ascending),
+                                         ctypes.byref(c)), "bitonic_sort_typed")
     return a, c
 
 

@@ -28,7 +28,12 @@
  *     0xFFFFFFFF keys (pairs: key 0xFFFFFFFF and index n..N-1);
  *   - descending keys-only flips every block's direction, so the pads end up
  *     first and the result is the last n positions; descending pairs sort
- *     (~key, index) ascending.
+ *     (~key, index) ascending;
+ *   - other key types (int32, float32, uint64, int64, float64) use the same
+ *     network with the type's own order: signed integers numerically, floats
+ *     by IEEE 754-2008 totalOrder (clause 5.10: -NaN < -inf < ... < -0 < +0
+ *     < ... < +inf < +NaN, NaNs ordered by payload), which fixes where
+ *     signed zeros and NaNs go; pads are the type's last key.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -420,6 +425,124 @@ int oracle_same_multiset_u32(const uint32_t *a, const uint32_t *b, uint64_t n)
     free(slot_cnt);
     free(used);
     return same;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Other key types: the same Section 3.1 network, with each type's order     */
+/* written out from its definition (no bit tricks).                           */
+/* ------------------------------------------------------------------------ */
+
+#define ORACLE_KEY_I32 1
+#define ORACLE_KEY_F32 2
+#define ORACLE_KEY_U64 3
+#define ORACLE_KEY_I64 4
+#define ORACLE_KEY_F64 5
+
+/* IEEE 754-2008 totalOrder (clause 5.10) as a strict "x before y":
+ *   - a key with the sign bit set comes before one without it (so -0 before
+ *     +0, and a negative NaN before everything, a positive NaN after);
+ *   - same sign, neither a NaN: the numeric order (equal zeros tie);
+ *   - same sign, NaNs: a NaN lies beyond every number on its sign's side,
+ *     and between two NaNs the larger payload lies further out. */
+static int f64_before(double x, double y, uint64_t bx, uint64_t by, uint64_t sign)
+{
+    int sx = (bx & sign) != 0, sy = (by & sign) != 0;
+    if (sx != sy) {
+#if ORACLE_MUTANT == 7
+        if (x == y) return 0;                /* planted: -0 and +0 tie */
+#endif
+        return sx;
+    }
+    int nx = x != x, ny = y != y;
+    if (!nx && !ny) return x < y;
+    uint64_t mx = bx & ~sign, my = by & ~sign;
+    if (nx && ny) return sx ? mx > my : mx < my;
+    /* exactly one NaN: it lies outward on its side */
+    return sx ? nx : ny;
+}
+
+static int typed_before(const void *x, const void *y, int type)
+{
+    switch (type) {
+    case ORACLE_KEY_I32: return *(const int32_t *)x < *(const int32_t *)y;
+    case ORACLE_KEY_U64: return *(const uint64_t *)x < *(const uint64_t *)y;
+    case ORACLE_KEY_I64: return *(const int64_t *)x < *(const int64_t *)y;
+    case ORACLE_KEY_F32: {
+        float fx, fy;
+        uint32_t bx, by;
+        memcpy(&fx, x, 4); memcpy(&fy, y, 4); memcpy(&bx, x, 4); memcpy(&by, y, 4);
+        /* the numbers compare exactly as doubles; the sign and the NaN
+           payloads come from the float's own bits (placed in the top half),
+           which the conversion cannot disturb */
+        return f64_before(fx, fy, (uint64_t)bx << 32, (uint64_t)by << 32, 1ull << 63);
+    }
+    case ORACLE_KEY_F64: {
+        double dx, dy;
+        uint64_t bx, by;
+        memcpy(&dx, x, 8); memcpy(&dy, y, 8); memcpy(&bx, x, 8); memcpy(&by, y, 8);
+        return f64_before(dx, dy, bx, by, 1ull << 63);
+    }
+    }
+    return 0;
+}
+
+static size_t typed_size(int type)
+{
+    return (type == ORACLE_KEY_I32 || type == ORACLE_KEY_F32) ? 4 : 8;
+}
+
+/* The last key of the type's order (pad value): the largest integer, or the
+ * positive NaN with the largest payload. */
+static void typed_max(unsigned char *out, int type)
+{
+    switch (type) {
+    case ORACLE_KEY_I32: { int32_t v = INT32_MAX; memcpy(out, &v, 4); break; }
+    case ORACLE_KEY_F32: { uint32_t v = 0x7FFFFFFFu; memcpy(out, &v, 4); break; }
+    case ORACLE_KEY_U64: { uint64_t v = UINT64_MAX; memcpy(out, &v, 8); break; }
+    case ORACLE_KEY_I64: { int64_t v = INT64_MAX; memcpy(out, &v, 8); break; }
+    default:             { uint64_t v = 0x7FFFFFFFFFFFFFFFull; memcpy(out, &v, 8); break; }
+    }
+}
+
+/* Section 3.1 network on keys of another type; same block directions, same
+ * padding and descending reading as oracle_bitonic_sort_u32. */
+int oracle_bitonic_sort_typed(void *keys, uint64_t n, int type, int ascending, oracle_counts *counts)
+{
+    oracle_counts local = {0, 0, 0};
+    if (!counts) counts = &local;
+    memset(counts, 0, sizeof(*counts));
+    if (type < ORACLE_KEY_I32 || type > ORACLE_KEY_F64) return ORACLE_ERR_INVALID;
+    if (n == 0) return ORACLE_OK;
+    if (!keys) return ORACLE_ERR_INVALID;
+    const size_t es = typed_size(type);
+    uint64_t N = next_pow2_u64(n);
+    unsigned char *a = (unsigned char *)malloc(N * es), tmp[8];
+    if (!a) return ORACLE_ERR_NOMEM;
+    memcpy(a, keys, n * es);
+    for (uint64_t i = n; i < N; ++i) typed_max(a + i * es, type);
+    int k = log2_u64(N);
+    for (int p = 1; p <= k; ++p) {
+        counts->phases += 1;
+        for (int j = p - 1; j >= 0; --j) {
+            uint64_t d = (uint64_t)1 << j;
+            counts->steps += 1;
+            for (uint64_t i = 0; i < N; ++i) {
+                if (i & d) continue;
+                unsigned char *x = a + i * es, *y = a + (i | d) * es;
+                int up = block_ascending(i, p, k, ascending, 0);
+                int out_of_order = up ? typed_before(y, x, type) : typed_before(x, y, type);
+                if (out_of_order) {
+                    memcpy(tmp, x, es);
+                    memcpy(x, y, es);
+                    memcpy(y, tmp, es);
+                }
+                counts->compare_exchanges += 1;
+            }
+        }
+    }
+    memcpy(keys, ascending ? a : a + (N - n) * es, n * es);
+    free(a);
+    return ORACLE_OK;
 }
 
 int oracle_mutant_id(void) { return ORACLE_MUTANT; }

@@ -202,9 +202,38 @@ def test_input_generators_shapes():
     assert 0.25 < hv.mean() < 0.35
 
 
+TYPED = {"f32": (np.float32, np.uint32), "f64": (np.float64, np.uint64), "i32": (np.int32, np.uint32),
+         "i64": (np.int64, np.uint64), "u64": (np.uint64, np.uint64)}
+
+
+def golden_order(name):
+    """Ascending keys of one golden line, as an array of the key type."""
+    dt, bits = TYPED[name]
+    (vals,) = read_golden("ieee754_total_order.txt")["order_" + name]
+    return np.array([int(v, 16) for v in vals], dtype=bits).view(dt)
+
+
+def check_golden_order(name, lib=None):
+    a = golden_order(name)
+    _, bits = TYPED[name]
+    for seed in range(3):
+        rng = np.random.default_rng(seed)
+        counts = rng.integers(1, 4, size=a.size)
+        want = np.repeat(a, counts)
+        x = want[rng.permutation(want.size)]
+        up = oracle.bitonic_sort_typed(x, True, lib=lib)[0]
+        down = oracle.bitonic_sort_typed(x, False, lib=lib)[0]
+        if not (np.array_equal(up.view(bits), want.view(bits)) and
+                np.array_equal(down.view(bits), want[::-1].view(bits))):
+            return False
+    return True
+
+
 def pin_battery(lib):
     """Returns the names of pins that fail for the oracle library ``lib``."""
     failed = []
+    if not check_golden_order("f32", lib) or not check_golden_order("f64", lib):
+        failed.append("ieee_total_order")
     for m in (4, 5, 8):
         if oracle.zero_one_failures(m, True, lib=lib) or oracle.zero_one_failures(m, False, lib=lib):
             failed.append(f"zero_one_{m}")
@@ -228,8 +257,41 @@ def test_pin_battery_passes_on_the_oracle():
     assert pin_battery(oracle.load()) == []
 
 
-@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7])
 def test_planted_mistakes_are_caught(mutant, tmp_path):
     lib = oracle.load(mutant=mutant, out_dir=str(tmp_path))
     assert lib.oracle_mutant_id() == mutant
     assert pin_battery(lib), f"mutant {mutant} passed every pin"
+
+
+@pytest.mark.parametrize("name", sorted(TYPED))
+def test_typed_orders_from_definitions(name):
+    # IEEE 754-2008 clause 5.10 (floats) and two's-complement / unsigned
+    # numeric order (integers), written out in tests/golden.
+    assert check_golden_order(name)
+
+
+@pytest.mark.parametrize("name", sorted(TYPED))
+@pytest.mark.parametrize("n", [1, 2, 3, 100, 1000, 4097])
+def test_typed_network_equals_library_sort(name, n):
+    # Without NaNs and negative zeros, every type's order is numpy's.
+    dt, bits = TYPED[name]
+    rng = np.random.default_rng(n)
+    raw = rng.integers(0, 2**63, size=n, dtype=np.uint64) * 2 + rng.integers(0, 2, size=n, dtype=np.uint64)
+    x = raw.astype(bits).view(dt) if np.dtype(bits).itemsize == 8 else (raw >> np.uint64(32)).astype(bits).view(dt)
+    if np.dtype(dt).kind == "f":
+        x = np.where(np.isnan(x) | ((x == 0) & np.signbit(x)), dt(1.25), x).astype(dt)
+        x[:: 7] = np.inf
+        x[3:: 11] = -np.inf
+    for asc in (True, False):
+        got, c = oracle.bitonic_sort_typed(x, asc)
+        want = np.sort(x) if asc else np.sort(x)[::-1]
+        assert np.array_equal(got.view(bits), want.view(bits)), (name, n, asc)
+        N = 1 << max(0, (n - 1).bit_length())
+        k = N.bit_length() - 1
+        assert c.compare_exchanges == N * k * (k + 1) // 4    # Section 3.2
+
+
+def test_typed_rejects_other_types():
+    with pytest.raises(TypeError):
+        oracle.bitonic_sort_typed(np.arange(4, dtype=np.int16))
