@@ -74,6 +74,28 @@ typedef enum {
 bitonic_status bitonic_sort_u32(uint32_t *keys, size_t n, int ascending, bitonic_stream_t stream);
 
 /*
+ * Keys-only sorts of other key types: the same network on the type's own
+ * order.  The paper sorts 32-bit integers (Section 5) and names other data
+ * types as future work (Section 6); these extend it.
+ *   int32 / int64   two's-complement numeric order;
+ *   float / double  IEEE 754-2008 totalOrder (clause 5.10):
+ *                   -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN, NaNs of
+ *                   one sign ordered by payload; bit patterns are preserved;
+ *   uint64          unsigned numeric order.
+ * Arguments as for bitonic_sort_u32: device pointer, sorted in place, work
+ * enqueued on `stream`.  keys must be aligned to the key size
+ * (BITONIC_ERR_INVALID otherwise); n up to 2^31 keys (BITONIC_ERR_UNSUPPORTED
+ * beyond).  The map to unsigned order is fused into the first load and the
+ * last store of the launch sequence (a separate pass only for the basic
+ * variant and for floats under the pipelined option).
+ */
+bitonic_status bitonic_sort_i32(int32_t *keys, size_t n, int ascending, bitonic_stream_t stream);
+bitonic_status bitonic_sort_f32(float *keys, size_t n, int ascending, bitonic_stream_t stream);
+bitonic_status bitonic_sort_u64(uint64_t *keys, size_t n, int ascending, bitonic_stream_t stream);
+bitonic_status bitonic_sort_i64(int64_t *keys, size_t n, int ascending, bitonic_stream_t stream);
+bitonic_status bitonic_sort_f64(double *keys, size_t n, int ascending, bitonic_stream_t stream);
+
+/*
  * Sorts key/value pairs in place.  Keys compare first; equal keys keep their
  * original index order (ascending index in both directions), so the result is
  * unique.  vals[i] travels with keys[i].  Uses a workspace of 8 * N bytes

@@ -29,8 +29,14 @@ EXPORTS = (
     "bitonic_last_device_error", "bitonic_release_workspace", "bitonic_set_options",
     "bitonic_get_options", "bitonic_plan_info", "bitonic_sort_u32_profiled", "bitonic_debug_plan",
     "bitonic_debug_desc_size", "bitonic_sort_pairs_u32_noalloc", "bitonic_sort_segmented_pairs_u32_bounded",
-    "bitonic_set_class_options",
+    "bitonic_set_class_options", "bitonic_sort_i32", "bitonic_sort_f32", "bitonic_sort_u64", "bitonic_sort_i64",
+    "bitonic_sort_f64",
 )
+
+# torch dtype name -> C entry point of the keys-only sorts (uint64 keys may be
+# held in an int64 tensor: pass key_type="uint64")
+KEY_TYPE_ENTRY = {"int32": "bitonic_sort_i32", "float32": "bitonic_sort_f32", "uint64": "bitonic_sort_u64",
+                  "int64": "bitonic_sort_i64", "float64": "bitonic_sort_f64", "uint32": "bitonic_sort_u32"}
 
 
 class BitonicError(RuntimeError):
@@ -62,6 +68,8 @@ def load() -> ctypes.CDLL:
     vp, sz, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
     pint = ctypes.POINTER(ctypes.c_int)
     lib.bitonic_sort_u32.argtypes = [vp, sz, i32, vp]
+    for name in ("bitonic_sort_i32", "bitonic_sort_f32", "bitonic_sort_u64", "bitonic_sort_i64", "bitonic_sort_f64"):
+        getattr(lib, name).argtypes = [vp, sz, i32, vp]
     lib.bitonic_sort_pairs_u32.argtypes = [vp, vp, sz, i32, vp]
     lib.bitonic_sort_segmented_u32.argtypes = [vp, vp, i32, vp]
     lib.bitonic_sort_segmented_pairs_u32.argtypes = [vp, vp, vp, i32, vp]
@@ -126,6 +134,24 @@ def sort_(keys, ascending: bool = True, stream=None):
     """Sorts a CUDA tensor of 32-bit keys in place (unsigned order)."""
     _check(load().bitonic_sort_u32(_u32_ptr(keys, "keys"), keys.numel(), int(bool(ascending)),
                                    _stream_handle(stream)), "bitonic_sort_u32")
+    return keys
+
+
+def sort_typed_(keys, ascending: bool = True, stream=None, key_type: str | None = None):
+    """Sorts a CUDA tensor in place by its element type's order: int32,
+    float32, int64, float64 (floats: IEEE 754 totalOrder), uint32 / uint64
+    (key_type "uint32" for an int32 tensor holding unsigned keys, "uint64"
+    for an int64 tensor)."""
+    if not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous CUDA tensor")
+    kt = key_type or str(keys.dtype).replace("torch.", "")
+    entry = KEY_TYPE_ENTRY.get(kt)
+    if entry is None:
+        raise ValueError(f"unsupported key type {kt}")
+    if keys.element_size() != (8 if kt in ("uint64", "int64", "float64") else 4):
+        raise ValueError(f"{kt} keys need {8 if '64' in kt else 4}-byte elements")
+    _check(getattr(load(), entry)(keys.data_ptr(), keys.numel(), int(bool(ascending)), _stream_handle(stream)),
+           entry)
     return keys
 
 

@@ -257,17 +257,84 @@ bitonic_status get_plan(DeviceState& ds, uint64_t nv, int key_bytes, PlanEntry**
 }
 
 // Enqueues the plan's launches on `s`.  events / kinds are optional.
+// Key types of the keys-only sorts.  The network always sorts ascending on
+// unsigned integers; every other type and direction reaches that order by an
+// order-preserving map on the first load and its inverse on the last store
+// (KeyMapHost; the device side is KeyMap in engine.cuh).
+enum KeyType { KEY_U32 = 0, KEY_I32 = 1, KEY_F32 = 2, KEY_U64 = 3, KEY_I64 = 4, KEY_F64 = 5 };
+
+struct KeyMaps {
+    KeyMapHost in, out;
+};
+
+int key_type_bytes(int type) { return type >= KEY_U64 ? 8 : 4; }
+
+// Maps for a type and direction, on keys of w bits (sign = the top bit):
+//   unsigned       v ^ b, b = 0 (ascending) or all ones (descending);
+//   signed         v ^ b, b = sign (ascending) or ~sign (descending);
+//   IEEE 754 float v ^ (fill(v) & ~sign) ^ sign: negative keys have every bit
+//                  flipped, non-negative ones the sign bit, so totalOrder
+//                  becomes unsigned order; descending also complements.
+//                  The inverse reads the sign from ~v (s = all ones).
+KeyMaps key_maps(int type, int ascending)
+{
+    const int w = 8 * key_type_bytes(type);
+    const uint64_t ones = w == 64 ? ~0ull : 0xFFFFFFFFull;
+    const uint64_t sign = 1ull << (w - 1);
+    KeyMaps m;
+    switch (type) {
+    case KEY_U32:
+    case KEY_U64:
+        m.in.b = m.out.b = ascending ? 0 : ones;
+        break;
+    case KEY_I32:
+    case KEY_I64:
+        m.in.b = m.out.b = ascending ? sign : (ones & ~sign);
+        break;
+    default:  // floats
+        m.in.a = m.out.a = ones & ~sign;
+        m.in.b = ascending ? sign : (ones & ~sign);
+        m.out.b = ascending ? sign : 0;
+        m.out.s = ones;
+        break;
+    }
+    return m;
+}
+
 bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* base, uint32_t lo, uint32_t hi,
-                            int desc, int key_bytes, int* status, cudaStream_t s, cudaEvent_t* events, int* kinds)
+                            const KeyMaps& km, int key_bytes, int* status, cudaStream_t s, cudaEvent_t* events,
+                            int* kinds)
 {
     const Plan& pl = pe.plan;
+    const uint64_t ones = key_bytes == 8 ? ~0ull : 0xFFFFFFFFull;
+    const bool xor_only = km.in.a == 0 && km.out.a == 0;
+    const bool steps = !pl.launches.empty() && pl.launches[0].kind == KIND_STEP;
+    const bool piped = pe.opt.pipeline && ds.pipe_blocks[pl.cfg] > 0 && status;
+    // The one-step kernels run ascending or descending on raw 4-byte keys
+    // themselves; the pipelined kernels take XOR masks.  Any other map runs
+    // as a separate elementwise pass before the first and after the last
+    // launch.
+    int step_desc = 0;
+    bool separate = false;
+    if (steps) {
+        const bool plain = xor_only && km.in.b == km.out.b && (km.in.b == 0 || (km.in.b == ones && key_bytes == 4));
+        if (plain) step_desc = km.in.b != 0;
+        else separate = true;
+    } else if (piped && !xor_only) {
+        separate = true;
+    }
+    const KeyMapHost ident;
+    if (separate) {
+        cudaError_t e = launch_keymap(key_bytes, base, lo, hi, km.in, s);
+        if (e != cudaSuccess) return cuda_fail(e, "key map launch");
+    }
     for (size_t i = 0; i < pl.launches.size(); ++i) {
         const Launch& L = pl.launches[i];
         if (events) BT_CK(cudaEventRecord(events[i], s));
         if (kinds) kinds[i] = L.kind;
         cudaError_t e;
         if (L.kind == KIND_STEP) {
-            e = launch_step(key_bytes, desc, base, lo, hi, (uint32_t)pl.N, L.hi, L.flip, s);
+            e = launch_step(key_bytes, step_desc, base, lo, hi, (uint32_t)pl.N, L.hi, L.flip, s);
         } else {
             const TileParams* hP = L.small ? &pl.small[L.desc] : nullptr;
             const TileParamsBig* dP = L.small ? nullptr : pe.d_descs + L.desc;
@@ -277,24 +344,28 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
                 const uint64_t live = ((uint64_t)hi + (1u << D.m) - 1) >> D.m;
                 if (live < ntiles) ntiles = (uint32_t)live;
             }
-            // A descending sort runs ascending on ~key: complement on the
-            // first load and the last store.
-            const int cin = desc && i == 0, cout = desc && i + 1 == pl.launches.size();
-            const int per_sm = ds.pipe_blocks[pl.cfg];
-            if (pe.opt.pipeline && per_sm > 0 && status) {
+            // The key maps are fused into the first load and the last store.
+            const KeyMapHost& mi = (i == 0 && !separate) ? km.in : ident;
+            const KeyMapHost& mo = (i + 1 == pl.launches.size() && !separate) ? km.out : ident;
+            if (piped) {
+                const int per_sm = ds.pipe_blocks[pl.cfg];
                 uint64_t g = (uint64_t)per_sm * ds.num_sms;
                 const uint32_t grid = (uint32_t)(g < ntiles ? g : ntiles);
-                e = launch_pipe(pe.opt.pipeline, pl.cfg, base, lo, hi, hP, dP, ntiles, grid, cin, cout, status, s);
+                e = launch_pipe(pe.opt.pipeline, pl.cfg, base, lo, hi, hP, dP, ntiles, grid, mi.b, mo.b, status, s);
             } else {
                 const uint32_t pf = pe.opt.l2_prefetch > 0
                                         ? (uint32_t)(pe.opt.l2_prefetch * ds.tile_blocks[pl.cfg] * ds.num_sms)
                                         : 0u;
-                e = launch_tile(pl.cfg, base, lo, hi, hP, dP, ntiles, cin, cout, s, pf);
+                e = launch_tile(pl.cfg, base, lo, hi, hP, dP, ntiles, mi, mo, s, pf);
             }
         }
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     }
     if (events) BT_CK(cudaEventRecord(events[pl.launches.size()], s));
+    if (separate) {
+        cudaError_t e = launch_keymap(key_bytes, base, lo, hi, km.out, s);
+        if (e != cudaSuccess) return cuda_fail(e, "key map launch");
+    }
     return BITONIC_OK;
 }
 
@@ -334,40 +405,44 @@ bitonic_status run_graphed(DeviceState& ds, const GraphKey& key, cudaStream_t us
     return BITONIC_OK;
 }
 
-bitonic_status check_keys_ptr(const void* p)
+bitonic_status check_keys_ptr(const void* p, int key_bytes = 4)
 {
-    if (!p || ((uintptr_t)p & 3u)) {
+    if (!p || ((uintptr_t)p & (uintptr_t)(key_bytes - 1))) {
         t_last_error = "null or misaligned pointer";
         return BITONIC_ERR_INVALID;
     }
     return BITONIC_OK;
 }
 
-bitonic_status sort_u32_impl(uint32_t* keys, size_t n, int ascending, cudaStream_t s, cudaEvent_t* events,
-                             int nevents, int* kinds)
+// Keys-only sort of any key type, in place on the caller's stream.
+bitonic_status sort_keys_impl(void* keys, size_t n, int type, int ascending, cudaStream_t s, cudaEvent_t* events,
+                              int nevents, int* kinds)
 {
     if (n > kMaxKeys) return BITONIC_ERR_UNSUPPORTED;
     if (n <= 1) return BITONIC_OK;
-    bitonic_status st = check_keys_ptr(keys);
+    const int kb = key_type_bytes(type);
+    bitonic_status st = check_keys_ptr(keys, kb);
     if (st) return st;
-    const uint32_t front = (uint32_t)(((uintptr_t)keys & 15u) / 4u);
+    // virtual front padding back to the 16-byte boundary before the keys
+    const uint32_t front = (uint32_t)(((uintptr_t)keys & 15u) / (uintptr_t)kb);
     const uint64_t nv = (uint64_t)n + front;
     if (nv > kMaxKeys) return BITONIC_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> g(g_mu);
     DeviceState* ds;
     if ((st = device_state(&ds))) return st;
     PlanEntry* pe;
-    if ((st = get_plan(*ds, nv, 4, &pe))) return st;
-    uint32_t* base = keys - front;
-    const int desc = ascending ? 0 : 1;
+    if ((st = get_plan(*ds, nv, kb, &pe))) return st;
+    void* base = (char*)keys - (size_t)front * kb;
+    const KeyMaps km = key_maps(type, ascending);
     int* status = ds->status;
     if (events) {
         if (nevents < (int)pe->plan.launches.size() + 1) return BITONIC_ERR_INVALID;
-        return enqueue_plan(*ds, *pe, base, front, (uint32_t)nv, desc, 4, status, s, events, kinds);
+        return enqueue_plan(*ds, *pe, base, front, (uint32_t)nv, km, kb, status, s, events, kinds);
     }
-    GraphKey key{0, n, desc, (uintptr_t)keys, 0, 0, 0, 0, 0, options_code(pe->opt), 0};
+    GraphKey key{type == KEY_U32 ? 0 : 20 + type, n, ascending ? 0 : 1, (uintptr_t)keys, 0, 0, 0, 0, 0,
+                 options_code(pe->opt), 0};
     return run_graphed(*ds, key, s, [&](cudaStream_t cs) {
-        return enqueue_plan(*ds, *pe, base, front, (uint32_t)nv, desc, 4, status, cs, nullptr, nullptr);
+        return enqueue_plan(*ds, *pe, base, front, (uint32_t)nv, km, kb, status, cs, nullptr, nullptr);
     });
 }
 
@@ -391,7 +466,7 @@ bitonic_status sort_pairs_impl(uint32_t* keys, uint32_t* vals, size_t n, int asc
                  options_code(pe->opt), 0};
     return run_graphed(*ds, key, s, [&](cudaStream_t cs) -> bitonic_status {
         BT_CK(launch_pairs_pack(comp, keys, nn, desc, cs));
-        bitonic_status st2 = enqueue_plan(*ds, *pe, comp, 0, nn, 0, 8, ds->status, cs, nullptr, nullptr);
+        bitonic_status st2 = enqueue_plan(*ds, *pe, comp, 0, nn, KeyMaps{}, 8, ds->status, cs, nullptr, nullptr);
         if (st2) return st2;
         BT_CK(launch_pairs_gather(comp, vals, nn, cs));
         BT_CK(launch_pairs_unpack(comp, keys, vals, nn, desc, cs));
@@ -471,7 +546,32 @@ extern "C" {
 
 bitonic_status bitonic_sort_u32(uint32_t* keys, size_t n, int ascending, bitonic_stream_t stream)
 {
-    return sort_u32_impl(keys, n, ascending, (cudaStream_t)stream, nullptr, 0, nullptr);
+    return sort_keys_impl(keys, n, KEY_U32, ascending, (cudaStream_t)stream, nullptr, 0, nullptr);
+}
+
+bitonic_status bitonic_sort_i32(int32_t* keys, size_t n, int ascending, bitonic_stream_t stream)
+{
+    return sort_keys_impl(keys, n, KEY_I32, ascending, (cudaStream_t)stream, nullptr, 0, nullptr);
+}
+
+bitonic_status bitonic_sort_f32(float* keys, size_t n, int ascending, bitonic_stream_t stream)
+{
+    return sort_keys_impl(keys, n, KEY_F32, ascending, (cudaStream_t)stream, nullptr, 0, nullptr);
+}
+
+bitonic_status bitonic_sort_u64(uint64_t* keys, size_t n, int ascending, bitonic_stream_t stream)
+{
+    return sort_keys_impl(keys, n, KEY_U64, ascending, (cudaStream_t)stream, nullptr, 0, nullptr);
+}
+
+bitonic_status bitonic_sort_i64(int64_t* keys, size_t n, int ascending, bitonic_stream_t stream)
+{
+    return sort_keys_impl(keys, n, KEY_I64, ascending, (cudaStream_t)stream, nullptr, 0, nullptr);
+}
+
+bitonic_status bitonic_sort_f64(double* keys, size_t n, int ascending, bitonic_stream_t stream)
+{
+    return sort_keys_impl(keys, n, KEY_F64, ascending, (cudaStream_t)stream, nullptr, 0, nullptr);
 }
 
 bitonic_status bitonic_sort_pairs_u32(uint32_t* keys, uint32_t* vals, size_t n, int ascending,
@@ -663,7 +763,7 @@ bitonic_status bitonic_sort_u32_profiled(uint32_t* keys, size_t n, int ascending
                                          bitonic_event_t* events, int nevents, int* kinds)
 {
     if (!events) return BITONIC_ERR_INVALID;
-    return sort_u32_impl(keys, n, ascending, (cudaStream_t)stream, (cudaEvent_t*)events, nevents, kinds);
+    return sort_keys_impl(keys, n, KEY_U32, ascending, (cudaStream_t)stream, (cudaEvent_t*)events, nevents, kinds);
 }
 
 // Copies the plan of an n-key sort (key_bytes 4 or 8) for inspection:

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "desc.h"
 
 namespace bitonic {
@@ -197,6 +199,24 @@ __device__ __forceinline__ ulonglong2 regs_to_vec<uint64_t>(const uint64_t* r)
     return make_ulonglong2(r[0], r[1]);
 }
 
+// Order-preserving key map, applied to real keys on a sort's first load and
+// last store: v -> v ^ (fill(v ^ s) & a) ^ b, fill(x) = all ones if x's top
+// bit is set, else zero.  With a = 0 it is the XOR with b (b = ~0: the
+// complement that turns a descending sort into an ascending one; b = the
+// sign bit: signed integers).  Floats use a = ~sign bit, which flips the
+// magnitude bits of negative keys (IEEE 754 totalOrder becomes unsigned
+// order); the inverse map on the store takes s = ~0.
+template <typename K>
+struct KeyMap {
+    K a, b, s;
+    __device__ __forceinline__ K operator()(K v) const
+    {
+        using S = typename std::make_signed<K>::type;
+        const K fill = (K)((S)(v ^ s) >> (8 * sizeof(K) - 1));
+        return v ^ (fill & a) ^ b;
+    }
+};
+
 // The tile engine for one CTA.  LOG_R keys-per-thread bits, LOG_T thread bits.
 template <typename K, bool DESC, int LOG_R, int LOG_T>
 struct Tile {
@@ -223,7 +243,7 @@ struct Tile {
     // Global load in the load round's layout.  base points at virtual
     // position 0; positions [lo, hi) hold real keys, others are pads.
     __device__ __forceinline__ void load_global(const K* __restrict__ base, uint32_t lo, uint32_t hi,
-                                                const IoDesc& io, uint32_t g0, uint32_t x, K cm)
+                                                const IoDesc& io, uint32_t g0, uint32_t x, KeyMap<K> m)
     {
         const uint32_t gt = g0 ^ io_thread_global<LOG_T>(io, x);
         uint32_t gr[NREG];
@@ -236,19 +256,19 @@ struct Tile {
             if (pos >= lo && pos + VEC <= hi) {
                 vec_to_regs<K>(*reinterpret_cast<const Vec*>(base + pos), dst);
 #pragma unroll
-                for (int c = 0; c < VEC; ++c) dst[c] ^= cm;
+                for (int c = 0; c < VEC; ++c) dst[c] = m(dst[c]);
             } else {
 #pragma unroll
                 for (int c = 0; c < VEC; ++c) {
                     const uint32_t p = pos + c;
-                    dst[c] = p < lo ? kFrontPad : (p >= hi ? kTailPad : (K)(base[p] ^ cm));
+                    dst[c] = p < lo ? kFrontPad : (p >= hi ? kTailPad : m(base[p]));
                 }
             }
         }
     }
 
     __device__ __forceinline__ void store_global(K* __restrict__ base, uint32_t lo, uint32_t hi,
-                                                 const IoDesc& io, uint32_t g0, uint32_t x, K cm)
+                                                 const IoDesc& io, uint32_t g0, uint32_t x, KeyMap<K> m)
     {
         const uint32_t gt = g0 ^ io_thread_global<LOG_T>(io, x);
         uint32_t gr[NREG];
@@ -259,7 +279,7 @@ struct Tile {
             const uint32_t pos = gt ^ reg_local_index<NREG>(gr, v);
             K src[VEC];
 #pragma unroll
-            for (int c = 0; c < VEC; ++c) src[c] = r[v * VEC + c] ^ cm;
+            for (int c = 0; c < VEC; ++c) src[c] = m(r[v * VEC + c]);
             if (pos >= lo && pos + VEC <= hi) {
                 *reinterpret_cast<Vec*>(base + pos) = regs_to_vec<K>(src);
             } else if (pos + VEC > lo && pos < hi) {
@@ -287,7 +307,7 @@ struct Tile {
 
     // Global load / store for tiles that lie wholly inside [lo, hi).
     __device__ __forceinline__ void load_global_interior(const K* __restrict__ base, const IoDesc& io, uint32_t g0,
-                                                         uint32_t x, K cm)
+                                                         uint32_t x, KeyMap<K> m)
     {
         const uint32_t gt = g0 ^ io_thread_global<LOG_T>(io, x);
         uint32_t gr[NREG];
@@ -296,19 +316,26 @@ struct Tile {
 #pragma unroll
         for (int v = 0; v < NV; ++v)
             vec_to_regs<K>(*reinterpret_cast<const Vec*>(base + (gt ^ reg_local_index<NREG>(gr, v))), r + v * VEC);
-        if (cm) {
+        apply_map(m);
+    }
+
+    // Applies m to every register: nothing for the identity, one XOR per key
+    // when a = 0 (branches are uniform across the CTA).
+    __device__ __forceinline__ void apply_map(KeyMap<K> m)
+    {
+        if (m.a) {
 #pragma unroll
-            for (int i = 0; i < R; ++i) r[i] ^= cm;
+            for (int i = 0; i < R; ++i) r[i] = m(r[i]);
+        } else if (m.b) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) r[i] ^= m.b;
         }
     }
 
     __device__ __forceinline__ void store_global_interior(K* __restrict__ base, const IoDesc& io, uint32_t g0,
-                                                          uint32_t x, K cm)
+                                                          uint32_t x, KeyMap<K> m)
     {
-        if (cm) {
-#pragma unroll
-            for (int i = 0; i < R; ++i) r[i] ^= cm;
-        }
+        apply_map(m);
         const uint32_t gt = g0 ^ io_thread_global<LOG_T>(io, x);
         uint32_t gr[NREG];
 #pragma unroll

@@ -39,25 +39,37 @@ constexpr int kNumTileCfgs = 9;
 
 const TileCfg& tile_cfg(int id);
 
-// Tile launches; complement_in / complement_out complement the keys on load /
-// store (descending 4-byte sorts run ascending on ~key).
+// Host side of an order-preserving key map v -> v ^ (fill(v ^ s) & a) ^ b
+// (fill = all ones if the top bit is set), truncated to the key width at
+// launch; the device side is KeyMap in engine.cuh.  All zero: identity.
+struct KeyMapHost {
+    uint64_t a = 0, b = 0, s = 0;
+};
+
+// Tile launches; real keys pass through mi on load and mo on store.
 cudaError_t launch_tile(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
-                        const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
+                        const TileParamsBig* dP, uint32_t grid, const KeyMapHost& mi, const KeyMapHost& mo,
                         cudaStream_t s, uint32_t pf_dist = 0);
 cudaError_t launch_tile_u32(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
-                            const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
+                            const TileParamsBig* dP, uint32_t grid, const KeyMapHost& mi, const KeyMapHost& mo,
                             uint32_t pf_dist, cudaStream_t s);
 cudaError_t launch_tile_u64(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
-                            const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
+                            const TileParamsBig* dP, uint32_t grid, const KeyMapHost& mi, const KeyMapHost& mo,
                             uint32_t pf_dist, cudaStream_t s);
+// Applies a key map to base[lo, hi) in one elementwise pass (for launch
+// kinds that cannot fuse it: the one-step kernels, the pipelined kernels
+// with a float map).
+cudaError_t launch_keymap(int key_bytes, void* base, uint32_t lo, uint32_t hi, const KeyMapHost& m, cudaStream_t s);
 cudaError_t tile_blocks_per_sm_u32(int cfg, int* blocks);
 cudaError_t tile_blocks_per_sm_u64(int cfg, int* blocks);
 cudaError_t tile_blocks_per_sm(int cfg, int* blocks);
 cudaError_t init_tile_attributes_u32();
 cudaError_t init_tile_attributes_u64();
+// Pipelined tile launches; keys are XORed with xor_in on load and xor_out on
+// store (maps with a = 0 only).
 cudaError_t launch_pipe(int mode, int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
-                        const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, int complement_in,
-                        int complement_out, int* status, cudaStream_t s);
+                        const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, uint64_t xor_in,
+                        uint64_t xor_out, int* status, cudaStream_t s);
 cudaError_t init_pipe_attributes(int* blocks_per_sm);
 cudaError_t launch_step(int key_bytes, int desc, void* base, uint32_t lo, uint32_t hi, uint32_t N, int j,
                         int flip, cudaStream_t s);

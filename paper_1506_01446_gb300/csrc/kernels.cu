@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "engine.cuh"
 #include "kernel_cfg.h"
 
 namespace bitonic {
@@ -73,12 +74,32 @@ cudaError_t launch_step_t(K* base, uint32_t lo, uint32_t hi, uint32_t N, int j, 
 }  // namespace
 
 cudaError_t launch_tile(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
-                        const TileParamsBig* dP, uint32_t grid, int complement_in, int complement_out,
+                        const TileParamsBig* dP, uint32_t grid, const KeyMapHost& mi, const KeyMapHost& mo,
                         cudaStream_t s, uint32_t pf_dist)
 {
-    if (tile_cfg(cfg).key_bytes == 4)
-        return launch_tile_u32(cfg, base, lo, hi, hP, dP, grid, complement_in, complement_out, pf_dist, s);
-    return launch_tile_u64(cfg, base, lo, hi, hP, dP, grid, 0, 0, pf_dist, s);
+    if (tile_cfg(cfg).key_bytes == 4) return launch_tile_u32(cfg, base, lo, hi, hP, dP, grid, mi, mo, pf_dist, s);
+    return launch_tile_u64(cfg, base, lo, hi, hP, dP, grid, mi, mo, pf_dist, s);
+}
+
+// One elementwise pass of a key map over base[lo, hi).
+template <typename K>
+__global__ void __launch_bounds__(256) k_keymap(K* __restrict__ base, uint32_t lo, uint32_t hi, KeyMap<K> m)
+{
+    for (uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += gridDim.x * blockDim.x)
+        base[i] = m(base[i]);
+}
+
+cudaError_t launch_keymap(int key_bytes, void* base, uint32_t lo, uint32_t hi, const KeyMapHost& m, cudaStream_t s)
+{
+    if (hi <= lo) return cudaSuccess;
+    uint32_t grid = (hi - lo + 255) / 256;
+    if (grid > 4096) grid = 4096;
+    if (key_bytes == 4)
+        k_keymap<uint32_t><<<grid, 256, 0, s>>>((uint32_t*)base, lo, hi,
+                                                KeyMap<uint32_t>{(uint32_t)m.a, (uint32_t)m.b, (uint32_t)m.s});
+    else
+        k_keymap<uint64_t><<<grid, 256, 0, s>>>((uint64_t*)base, lo, hi, KeyMap<uint64_t>{m.a, m.b, m.s});
+    return cudaGetLastError();
 }
 
 // Resident CTAs per SM of a tile configuration (after init_tile_attributes).

@@ -156,7 +156,7 @@ __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uin
         __syncthreads();
         if (next < ntiles) issue(next);
         run_tile_rounds<K, DESC, LOG_R, LOG_T, CATALOG>(t, Y, P, x);
-        t.store_global(base, lo, hi, P.io[1], g0, x, cm_out);
+        t.store_global(base, lo, hi, P.io[1], g0, x, KeyMap<K>{K(0), cm_out, K(0)});
         __syncthreads();
     }
 }
@@ -179,11 +179,11 @@ k_pipe_big(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParamsBig* 
 
 template <typename K, int LR, int LT>
 cudaError_t launch_pipe_t(int mode, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
-                          const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, int ci, int co, int* status,
-                          cudaStream_t s)
+                          const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, uint64_t xor_in,
+                          uint64_t xor_out, int* status, cudaStream_t s)
 {
     constexpr size_t kSmem = PipeSmem<K, LR + LT>::kBytes;
-    const K cin = ci ? ~K(0) : K(0), cout = co ? ~K(0) : K(0);
+    const K cin = (K)xor_in, cout = (K)xor_out;
     if (mode == 2) {
         if (hP)
             k_pipe<1, K, LR, LT><<<grid, 1 << LT, kSmem, s>>>((K*)base, lo, hi, *hP, ntiles, cin, cout, status);
@@ -222,12 +222,12 @@ cudaError_t pipe_attr_t(int* blocks_per_sm)
 }  // namespace
 
 cudaError_t launch_pipe(int mode, int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
-                        const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, int complement_in,
-                        int complement_out, int* status, cudaStream_t s)
+                        const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, uint64_t xor_in,
+                        uint64_t xor_out, int* status, cudaStream_t s)
 {
 #define BITONIC_PIPE_CASE(ID, KT, LR, LT, MB)                                                                 \
     case ID:                                                                                                \
-        return launch_pipe_t<KT, LR, LT>(mode, base, lo, hi, hP, dP, ntiles, grid, complement_in, complement_out, \
+        return launch_pipe_t<KT, LR, LT>(mode, base, lo, hi, hP, dP, ntiles, grid, xor_in, xor_out, \
                                          status, s);
     switch (cfg) {
         BITONIC_PIPE_CONFIGS(BITONIC_PIPE_CASE)

@@ -112,7 +112,7 @@ extern "C" bitonic_status bitonic_sort_pairs_u32_noalloc(uint32_t* keys, uint32_
             const uint64_t live = ((uint64_t)nn + (1u << D.m) - 1) >> D.m;
             if (live < ntiles) ntiles = (uint32_t)live;
         }
-        e = launch_tile(pl->cfg, d->comp, 0, nn, &pl->small[L.desc], nullptr, ntiles, 0, 0, s);
+        e = launch_tile(pl->cfg, d->comp, 0, nn, &pl->small[L.desc], nullptr, ntiles, KeyMapHost{}, KeyMapHost{}, s);
         if (e != cudaSuccess) return na_fail(e, "tile pass");
     }
     e = launch_pairs_gather(d->comp, vals, nn, s);

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "engine.cuh"
+#include "kernel_cfg.h"
 #include "patterns.h"
 #include "tma.cuh"
 
@@ -118,8 +119,8 @@ __device__ __forceinline__ void prefetch_tile_l2(const K* base, uint32_t lo, uin
 }
 
 template <typename K, bool DESC, int LOG_R, int LOG_T, bool CATALOG, class PT>
-__device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uint32_t hi, const PT& P, K cm_in,
-                                          K cm_out, uint32_t pf_dist = 0)
+__device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uint32_t hi, const PT& P,
+                                          KeyMap<K> m_in, KeyMap<K> m_out, uint32_t pf_dist = 0)
 {
     using T = Tile<K, DESC, LOG_R, LOG_T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -130,52 +131,54 @@ __device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uin
     const bool interior = (g0 & ~P.span_mask) >= lo && (g0 | P.span_mask) < hi;
     T t;
     if (interior)
-        t.load_global_interior(base, P.io[0], g0, x, cm_in);
+        t.load_global_interior(base, P.io[0], g0, x, m_in);
     else
-        t.load_global(base, lo, hi, P.io[0], g0, x, cm_in);
+        t.load_global(base, lo, hi, P.io[0], g0, x, m_in);
     prefetch_tile_l2<K, LOG_T>(base, lo, hi, P, pf_dist);
     run_tile_rounds<K, DESC, LOG_R, LOG_T, CATALOG>(t, sm, P, x);
     if (interior)
-        t.store_global_interior(base, P.io[1], g0, x, cm_out);
+        t.store_global_interior(base, P.io[1], g0, x, m_out);
     else
-        t.store_global(base, lo, hi, P.io[1], g0, x, cm_out);
+        t.store_global(base, lo, hi, P.io[1], g0, x, m_out);
 }
 
 // Descriptor passed by value: every thread reads it through the constant
-// bank.  Keys are complemented on load / store when cm_in / cm_out are all
-// ones (a descending sort runs as an ascending sort of ~key).  The round
+// bank.  Real keys pass through m_in on load and m_out on store (identity
+// maps except on a sort's first and last launch: the complement of a
+// descending sort, the order-preserving maps of signed and float keys).  The round
 // catalog (straight-line code per round shape) pays for its instruction
 // footprint with 4-byte keys (2^28: 13.5 vs 14.7 ms on GB300) but not with
 // 8-byte composites (2^26 pairs: 10.33 vs 10.22 ms), which use per-step
 // dispatch.
 template <typename K, int LOG_R, int LOG_T, int MINB>
 __global__ void __launch_bounds__(1 << LOG_T, MINB)
-k_tile(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P, K cm_in, K cm_out,
-       uint32_t pf_dist)
+k_tile(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P, KeyMap<K> m_in,
+       KeyMap<K> m_out, uint32_t pf_dist)
 {
-    tile_pass<K, false, LOG_R, LOG_T, sizeof(K) == 4>(base, lo, hi, P, cm_in, cm_out, pf_dist);
+    tile_pass<K, false, LOG_R, LOG_T, sizeof(K) == 4>(base, lo, hi, P, m_in, m_out, pf_dist);
 }
 
 // Descriptor with more rounds than fit by value, read from global memory.
 template <typename K, int LOG_R, int LOG_T, int MINB>
 __global__ void __launch_bounds__(1 << LOG_T, MINB)
-k_tile_big(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParamsBig* __restrict__ P, K cm_in, K cm_out)
+k_tile_big(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParamsBig* __restrict__ P, KeyMap<K> m_in,
+           KeyMap<K> m_out)
 {
-    tile_pass<K, false, LOG_R, LOG_T, false>(base, lo, hi, *P, cm_in, cm_out);
+    tile_pass<K, false, LOG_R, LOG_T, false>(base, lo, hi, *P, m_in, m_out);
 }
 
 // Launcher and attribute setup of one configuration.
 template <typename K, int LR, int LT, int MB>
 cudaError_t launch_tile_t(void* base, uint32_t lo, uint32_t hi, const TileParams* hP, const TileParamsBig* dP,
-                          uint32_t grid, int complement_in, int complement_out, uint32_t pf_dist, cudaStream_t s)
+                          uint32_t grid, const KeyMapHost& mi, const KeyMapHost& mo, uint32_t pf_dist, cudaStream_t s)
 {
     constexpr int kThreads = 1 << LT;
     constexpr size_t kSmem = (size_t(1) << (LR + LT)) * sizeof(K);
-    const K ci = complement_in ? ~K(0) : K(0), co = complement_out ? ~K(0) : K(0);
+    const KeyMap<K> ki{(K)mi.a, (K)mi.b, (K)mi.s}, ko{(K)mo.a, (K)mo.b, (K)mo.s};
     if (hP)
-        k_tile<K, LR, LT, MB><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, *hP, ci, co, pf_dist);
+        k_tile<K, LR, LT, MB><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, *hP, ki, ko, pf_dist);
     else
-        k_tile_big<K, LR, LT, MB><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, dP, ci, co);
+        k_tile_big<K, LR, LT, MB><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, dP, ki, ko);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,13 @@ def test_argument_errors_need_no_gpu():
     assert lib.bitonic_sort_segmented_u32(16, 16, 0, None) == bt.OK
     assert lib.bitonic_sort_segmented_pairs_u32(16, None, 16, 3, None) == bt.ERR_INVALID
     assert lib.bitonic_sort_u32_profiled(16, 100, 1, None, None, 0, None) == bt.ERR_INVALID
+    for name, size in (("bitonic_sort_i32", 4), ("bitonic_sort_f32", 4), ("bitonic_sort_u64", 8),
+                       ("bitonic_sort_i64", 8), ("bitonic_sort_f64", 8)):
+        f = getattr(lib, name)
+        assert f(None, 10, 1, None) == bt.ERR_INVALID, name
+        assert f(size // 2, 10, 1, None) == bt.ERR_INVALID, name        # not aligned to the key size
+        assert f(None, 1, 0, None) == bt.OK, name
+        assert f(16, (1 << 31) + 1, 1, None) == bt.ERR_UNSUPPORTED, name
 
 
 def test_options_validation():

@@ -260,3 +260,70 @@ def test_segmented_many_tiny_and_class_boundaries():
     check_segmented(keys, offs)
     keys2, offs2 = segments_case([l for l in lens if l <= 8192], seed=22)
     check_segmented(keys2, offs2, pairs=True)
+
+
+TYPED_TORCH = {"int32": "int32", "float32": "float32", "uint64": "int64", "int64": "int64", "float64": "float64"}
+
+
+def to_dev_typed(a: np.ndarray, pad_front: int = 0):
+    """numpy keys -> CUDA tensor with the same bits, starting pad_front keys
+    past an allocation boundary (so 4- and 8-byte keys can sit off a 16-byte
+    boundary)."""
+    dt = getattr(torch, TYPED_TORCH[a.dtype.name])
+    raw = np.zeros(a.size + pad_front, dtype=a.dtype)
+    raw[pad_front:] = a
+    host = torch.from_numpy(raw.view(np.int64 if a.dtype.itemsize == 8 else np.int32)).view(dt)
+    return host.cuda()[pad_front:]
+
+
+def typed_host(t, like: np.ndarray) -> np.ndarray:
+    return t.cpu().view(torch.int64 if like.dtype.itemsize == 8 else torch.int32).numpy().view(like.dtype)
+
+
+def check_typed(keys, ascending, pad_front=0):
+    t = to_dev_typed(keys, pad_front)
+    bt.sort_typed_(t, ascending, key_type=keys.dtype.name)
+    torch.cuda.synchronize()
+    got = typed_host(t, keys)
+    want = oracle.bitonic_sort_typed(keys, ascending)[0]
+    ubits = np.uint64 if keys.dtype.itemsize == 8 else np.uint32
+    assert np.array_equal(got.view(ubits), want.view(ubits)), (keys.dtype.name, keys.size, ascending, pad_front)
+
+
+@pytest.mark.parametrize("kind", workloads.TYPED_KEY_KINDS)
+@pytest.mark.parametrize("ascending", [True, False])
+def test_typed_keys_against_oracle(kind, ascending):
+    # Special values everywhere (signed zeros, infinities, NaNs of both signs
+    # and kinds, subnormals, integer extremes); sizes over several tiles with
+    # ragged tails, and a pointer off the 16-byte boundary.
+    for n in [2, 3, 7, 1000, 8193, 65537, (1 << 18) + 5]:
+        keys = workloads.typed_keys(kind, n, seed=n)
+        check_typed(keys, ascending)
+    check_typed(workloads.typed_keys(kind, 70001, seed=4), ascending, pad_front=1)
+
+
+@pytest.mark.parametrize("kind", workloads.TYPED_KEY_KINDS)
+def test_typed_keys_large_against_library_sort(kind):
+    # 2^24 keys (several global passes) without NaNs or -0, where numpy's
+    # order is the type's total order.
+    keys = workloads.typed_keys(kind, 1 << 24, seed=24, specials=False)
+    want = np.sort(keys)
+    ubits = np.uint64 if keys.dtype.itemsize == 8 else np.uint32
+    for asc in (True, False):
+        t = to_dev_typed(keys)
+        bt.sort_typed_(t, asc, key_type=kind)
+        torch.cuda.synchronize()
+        got = typed_host(t, keys)
+        assert np.array_equal(got.view(ubits), (want if asc else want[::-1]).view(ubits)), (kind, asc)
+
+
+@pytest.mark.parametrize("variant,pipeline", [(1, 0), (2, 0), (0, 1)])
+@pytest.mark.parametrize("kind", ["float32", "int32", "float64", "int64"])
+def test_typed_keys_other_variants(kind, variant, pipeline):
+    # The basic variant's one-step kernels and the pipelined kernels take the
+    # key map as separate passes (floats) or as XOR masks (signed integers).
+    bt.set_options(variant=variant, pipeline=pipeline)
+    for n in [5, 4097, 65537]:
+        keys = workloads.typed_keys(kind, n, seed=n + 11)
+        check_typed(keys, True)
+        check_typed(keys, False)

@@ -135,3 +135,45 @@ def serving_requests(count: int, seed: int, rate: float = 2000.0, lo_log2: int =
     sizes = np.clip(sizes, int(lo), int(hi))
     has_vals = uniform01(count, seed ^ 0x123457) < pair_frac
     return arrival, sizes, has_vals
+
+
+TYPED_KEY_KINDS = ("int32", "float32", "uint64", "int64", "float64")
+
+# Bit patterns every typed test mixes in: integer extremes; for floats the
+# signed zeros, infinities, subnormals and NaNs of both signs and kinds with
+# several payloads.
+_SPECIAL_BITS = {
+    "int32": [0x80000000, 0x80000001, 0xFFFFFFFF, 0, 1, 0x7FFFFFFE, 0x7FFFFFFF],
+    "float32": [0x00000000, 0x80000000, 0x7F800000, 0xFF800000, 0x00000001, 0x80000001, 0x007FFFFF,
+                0x7FC00000, 0xFFC00000, 0x7F800001, 0xFF800001, 0x7FFFFFFF, 0xFFFFFFFF, 0x7FC00123],
+    "uint64": [0, 1, 0x7FFFFFFFFFFFFFFF, 0x8000000000000000, 0xFFFFFFFFFFFFFFFF, 0xFFFFFFFF, 0x100000000],
+    "int64": [0x8000000000000000, 0xFFFFFFFFFFFFFFFF, 0, 1, 0x7FFFFFFFFFFFFFFF],
+    "float64": [0, 0x8000000000000000, 0x7FF0000000000000, 0xFFF0000000000000, 1, 0x8000000000000001,
+                0x7FF8000000000000, 0xFFF8000000000000, 0x7FF0000000000001, 0xFFF0000000000001,
+                0x7FFFFFFFFFFFFFFF, 0xFFFFFFFFFFFFFFFF],
+}
+_TYPED_DTYPES = {"int32": (np.int32, np.uint32), "float32": (np.float32, np.uint32),
+                 "uint64": (np.uint64, np.uint64), "int64": (np.int64, np.uint64),
+                 "float64": (np.float64, np.uint64)}
+
+
+def typed_keys(kind: str, n: int, seed: int, specials: bool = True) -> np.ndarray:
+    """n keys of a numpy dtype from uniform random bit patterns (for floats
+    that spans every binade, with a few NaNs and infinities).  specials:
+    scatter the kind's special bit patterns through the array (about 1 in 16
+    keys).  specials=False gives keys on which numpy's order is the type's
+    total order: no NaNs and no negative zeros (replaced by 1.0 and +0)."""
+    dt, bits = _TYPED_DTYPES[kind]
+    z = splitmix64(seed, n)
+    raw = (z >> np.uint64(32)).astype(np.uint32) if np.dtype(bits).itemsize == 4 else z
+    raw = raw.astype(bits)
+    if specials:
+        sp = np.array(_SPECIAL_BITS[kind], dtype=np.uint64).astype(bits)
+        pick = splitmix64(seed + 1, n)
+        where = (pick & np.uint64(15)) == 0
+        raw[where] = sp[(pick[where] >> np.uint64(8)) % np.uint64(sp.size)]
+    keys = raw.view(dt).copy()
+    if not specials and np.dtype(dt).kind == "f":
+        keys[np.isnan(keys)] = dt(1.0)
+        keys[(keys == 0) & np.signbit(keys)] = dt(0.0)
+    return keys
