@@ -51,6 +51,7 @@ def parse():
                     help="autotuner choices file: installed without measuring when it holds this size "
                          "(so a profiled run repeats a timed run's configuration), else written")
     ap.add_argument("--no-pairs", action="store_true", help="skip the key/value leg")
+    ap.add_argument("--no-key-types", action="store_true", help="skip the int32/float32/64-bit key leg")
     ap.add_argument("--ablation", action="store_true",
                     help="also time the paper's three GPU variants (Basic / Semi / Optimized) over its sizes")
     return ap.parse_args()
@@ -161,6 +162,43 @@ def pairs_leg(bt, torch, steps):
     return {"n": n, "ms": ms, "gpairs_s": n / ms / 1e6, "plan": info, "sampled_sorted": bool(np.all(out_k[1:] >= out_k[:-1]))}
 
 
+def key_types_leg(bt, torch, steps, peak_gbs):
+    """Keys-only sorts of the other key types, 512 MiB each (inputs larger
+    than L2): 2^27 int32 / float32 keys, 2^26 uint64 / int64 / float64 keys,
+    uniform random bit patterns without NaNs or -0 (so numpy can check the
+    sampled output), ascending."""
+    out = {}
+    stream = torch.cuda.current_stream()
+    for kind in workloads.TYPED_KEY_KINDS:
+        wide = kind in ("uint64", "int64", "float64")
+        n = 1 << (26 if wide else 27)
+        keys = workloads.typed_keys(kind, n, seed=workloads.SEEDS["key_types"], specials=False)
+        tdt = getattr(torch, {"uint64": "int64"}.get(kind, kind))
+        src = torch.from_numpy(keys.view(np.int64 if wide else np.int32)).view(tdt).cuda()
+        buf = src.clone()
+        for _ in range(2):
+            buf.copy_(src)
+            bt.sort_typed_(buf, key_type=kind)
+        times = []
+        for _ in range(steps):
+            buf.copy_(src)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bt.sort_typed_(buf, key_type=kind)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        ms = statistics.median(times)
+        sample = buf[:: 1 << 10].cpu().view(torch.int64 if wide else torch.int32).numpy().view(keys.dtype)
+        info = bt.plan_info(n, pairs=wide)
+        design_ms = info["hbm_passes"] * 2 * keys.dtype.itemsize * n / (peak_gbs * 1e6)
+        out[kind] = {"n": n, "ms": ms, "gkeys_s": n / ms / 1e6, "hbm_passes": info["hbm_passes"],
+                     "design_roofline_frac": design_ms / ms,
+                     "sampled_sorted": bool(np.all(sample[1:] >= sample[:-1]))}
+        del src, buf
+    return out
+
+
 def ablation_leg(bt, torch):
     """Section 5, Table 1 in shape: the Basic (one kernel per step, Section 3.3),
     Semi (shared memory, Section 4.1) and Optimized (registers too, Section 4.2)
@@ -169,7 +207,7 @@ def ablation_leg(bt, torch):
     rows = []
     for k in range(17, 29):
         n = 1 << k
-        src = torch.randint(-2**31, 2**31 - 1, (n,), dtype=torch.int32, device="cuda")
+        src = torch.from_numpy(workloads.uniform_u32(n, seed=k).view(np.int32)).cuda()
         buf = src.clone()
         row = {"n_log2": k}
         for name, var in (("basic", 1), ("semi", 2), ("optimized", 0)):
@@ -464,6 +502,8 @@ def main():
         assert np.all(out[1:] >= out[:-1])
     if not args.no_pairs and rank == 0:
         line["pairs"] = pairs_leg(bt, torch, max(3, args.steps))
+    if not args.no_key_types and rank == 0:
+        line["key_types"] = key_types_leg(bt, torch, max(3, args.steps), hbm_gbs)
     if args.ablation and rank == 0:
         line["ablation"] = ablation_leg(bt, torch)
     if not args.no_segmented and rank == 0:

@@ -1,7 +1,8 @@
 /*
  * bitonic.h -- C ABI of the GB300 (sm_103a) bitonic sorting library.
  *
- * The library sorts 32-bit unsigned keys, and key/value pairs, with Batcher's
+ * The library sorts 32-bit unsigned keys, key/value pairs, and keys of other
+ * types (int32, float, uint64, int64, double), with Batcher's
  * bitonic sorting network as described in "The implementation and
  * optimization of Bitonic sort algorithm based on CUDA" (Mu, Cui, Song;
  * arXiv 1506.01446):
@@ -17,7 +18,8 @@
  *
  * Conventions shared by every entry point
  *   - Pointers named keys / vals / offsets are DEVICE pointers owned by the
- *     caller; they must be at least 4-byte aligned.  Sorting is in place.
+ *     caller; they must be aligned to their element size (4 bytes, 8 for
+ *     64-bit keys).  Sorting is in place.
  *   - Work is enqueued on `stream` (NULL = the legacy default stream) and the
  *     call returns without waiting.  Argument errors are reported before
  *     anything is enqueued; CUDA launch errors as BITONIC_ERR_CUDA.
@@ -177,9 +179,8 @@ typedef struct {
                              bit 1: store straight from its last round's layout (instead of an
                              extra shared-memory transpose into a coalesced layout); 0 = off */
     int ctas_per_sm;      /* tile kernels: 3 = registers capped for three resident CTAs per SM
-                             where such a kernel exists for the tile shape, else uncapped;
-                             2 = uncapped (two CTAs); 0 = automatic (3 for 4-byte keys, 2 for
-                             pairs; default) */
+                             where such a kernel exists for the tile shape, else two;
+                             2 = registers bounded for two CTAs; 0 = automatic (3; default) */
     int min_row_log2;     /* shortest run of consecutive keys a multi-stride pass moves, log2
                              (keys); 0 = 128 bytes.  Shorter rows fit one more stride per pass. */
     int l2_prefetch;      /* > 0: each tile CTA asks the TMA unit to prefetch into L2 the tile

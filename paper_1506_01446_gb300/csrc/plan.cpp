@@ -299,10 +299,11 @@ int choose_cfg(int key_bytes, const Options& opt)
     // the largest configured value below that.
     const int pref_r = opt.keys_per_thread_log2 ? opt.keys_per_thread_log2 : (key_bytes == 4 ? 6 : 5);
     // Register cap: 3 = kernels capped for three resident CTAs per SM, 2 =
-    // uncapped, 0 = capped for 4-byte keys only (the capped composite kernel
-    // spills and loses).  A cap is taken where a capped kernel of this shape
-    // exists; other shapes fall back to the uncapped kernel.
-    const int cap = opt.ctas_per_sm ? opt.ctas_per_sm : (key_bytes == 4 ? 3 : 2);
+    // kernels bounded for two; 0 = automatic (three).  A cap is taken where
+    // a capped kernel of this shape exists; other shapes fall back to the
+    // two-CTA kernel.  (On GB300 at 2^26: 8-byte keys 8.8 ms capped against
+    // 11.9 ms two-CTA; 4-byte keys within 1-4% either way.)
+    const int cap = opt.ctas_per_sm ? opt.ctas_per_sm : 3;
     const int want_blocks = cap == 3 ? 3 : 1;
     for (int blocks : {want_blocks, 1}) {
         int best = -1;
@@ -315,7 +316,7 @@ int choose_cfg(int key_bytes, const Options& opt)
             if (c.log_r + c.log_t != tile) continue;
             if (opt.keys_per_thread_log2 && c.log_r != opt.keys_per_thread_log2) continue;
             if (c.log_r > pref_r) continue;
-            if (c.min_blocks != blocks) continue;
+            if ((c.min_blocks == 3) != (blocks == 3)) continue;
             if (best < 0 || c.log_r > kCfgs[best].log_r) best = i;
         }
         if (best >= 0) return best;

@@ -27,6 +27,7 @@ ALL_EQUAL_VALUE = 0x9E3779B9
 
 # Default seeds of the named workloads (any seed may be passed explicitly).
 SEEDS = {
+    "key_types": 1506_01446_6,
     "n16_uniform": 1506_01446,
     "n24": 2024,
     "n24_npow2": 10_000_019,
