@@ -98,6 +98,46 @@ bitonic_status bitonic_sort_i64(int64_t *keys, size_t n, int ascending, bitonic_
 bitonic_status bitonic_sort_f64(double *keys, size_t n, int ascending, bitonic_stream_t stream);
 
 /*
+ * bitonic_sort_u32 on HOST memory: sorts in[0..n) into out[0..n) (in may
+ * equal out).  The paper's timings include the transfers to and from the GPU
+ * (Section 5); this call owns them.
+ *   - Both pointers are host pointers (page-locked memory gives asynchronous
+ *     copies; pageable memory works but the copies then block the caller).
+ *   - Work is enqueued on `stream`; out is valid once the stream reaches
+ *     that point (synchronise before reading it).
+ *   - The keys pass through a per-stream device buffer of 4·n bytes (the
+ *     pair workspace, grown with cudaMalloc as needed).
+ *   - The upload runs in chunks on `stream`, and each chunk's tiles are
+ *     sorted on a library-owned second stream as soon as they arrive.  When
+ *     the last pass works on whole tiles, each chunk is downloaded as soon as
+ *     its tiles finish.  So the copies overlap the first and last passes.
+ *     (Sorts on different streams may run concurrently; for a stream of
+ *     arrays bitonic_sort_u32_host_batch overlaps copies with passes
+ *     without running two sorts at once.)
+ *   - BITONIC_ERR_INVALID for a null pointer when n > 0;
+ *     BITONIC_ERR_UNSUPPORTED while `stream` is being captured into a graph,
+ *     or for n > 2^31.
+ */
+bitonic_status bitonic_sort_u32_host(const uint32_t *in, uint32_t *out, size_t n, int ascending,
+                                     bitonic_stream_t stream);
+
+/*
+ * bitonic_sort_u32_host for count arrays in turn: in[j][0..n[j]) is sorted
+ * into out[j][0..n[j]) (host pointers; in[j] may equal out[j]; n[j] = 0
+ * skips array j).  The arrays alternate between two device buffers (the
+ * second one grown with cudaMalloc to the largest n[j]).  Uploads, passes and
+ * downloads run on three library-owned streams: array j+1's upload and
+ * array j-1's download overlap array j's passes, while the passes of two
+ * arrays never run at once.  `stream` waits for everything before the
+ * return; synchronise it before reading out[].  in, out and n are host
+ * arrays of count entries.  BITONIC_ERR_INVALID for count < 0 or a null
+ * array or pointer; BITONIC_ERR_UNSUPPORTED under graph capture or for
+ * n[j] > 2^31.
+ */
+bitonic_status bitonic_sort_u32_host_batch(const uint32_t *const *in, uint32_t *const *out, const size_t *n,
+                                           int count, int ascending, bitonic_stream_t stream);
+
+/*
  * Sorts key/value pairs in place.  Keys compare first; equal keys keep their
  * original index order (ascending index in both directions), so the result is
  * unique.  vals[i] travels with keys[i].  Uses a workspace of 8 * N bytes

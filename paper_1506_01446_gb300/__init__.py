@@ -30,7 +30,7 @@ EXPORTS = (
     "bitonic_get_options", "bitonic_plan_info", "bitonic_sort_u32_profiled", "bitonic_debug_plan",
     "bitonic_debug_desc_size", "bitonic_sort_pairs_u32_noalloc", "bitonic_sort_segmented_pairs_u32_bounded",
     "bitonic_set_class_options", "bitonic_sort_i32", "bitonic_sort_f32", "bitonic_sort_u64", "bitonic_sort_i64",
-    "bitonic_sort_f64",
+    "bitonic_sort_f64", "bitonic_sort_u32_host", "bitonic_sort_u32_host_batch",
 )
 
 # torch dtype name -> C entry point of the keys-only sorts (uint64 keys may be
@@ -70,6 +70,9 @@ def load() -> ctypes.CDLL:
     lib.bitonic_sort_u32.argtypes = [vp, sz, i32, vp]
     for name in ("bitonic_sort_i32", "bitonic_sort_f32", "bitonic_sort_u64", "bitonic_sort_i64", "bitonic_sort_f64"):
         getattr(lib, name).argtypes = [vp, sz, i32, vp]
+    lib.bitonic_sort_u32_host.argtypes = [vp, vp, sz, i32, vp]
+    lib.bitonic_sort_u32_host_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(sz), i32,
+                                                i32, vp]
     lib.bitonic_sort_pairs_u32.argtypes = [vp, vp, sz, i32, vp]
     lib.bitonic_sort_segmented_u32.argtypes = [vp, vp, i32, vp]
     lib.bitonic_sort_segmented_pairs_u32.argtypes = [vp, vp, vp, i32, vp]
@@ -153,6 +156,46 @@ def sort_typed_(keys, ascending: bool = True, stream=None, key_type: str | None 
     _check(getattr(load(), entry)(keys.data_ptr(), keys.numel(), int(bool(ascending)), _stream_handle(stream)),
            entry)
     return keys
+
+
+def sort_host(keys_in, keys_out=None, ascending: bool = True, stream=None):
+    """Sorts 32-bit keys held in HOST memory (CPU tensors; page-locked for
+    asynchronous copies) into keys_out (default: in place).  Work is
+    enqueued on the CUDA stream; synchronise before reading keys_out."""
+    if keys_out is None:
+        keys_out = keys_in
+    for t, name in ((keys_in, "keys_in"), (keys_out, "keys_out")):
+        if t.is_cuda or t.element_size() != 4 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous host tensor of 4-byte keys")
+    if keys_in.numel() != keys_out.numel():
+        raise ValueError("keys_in and keys_out differ in length")
+    _check(load().bitonic_sort_u32_host(keys_in.data_ptr(), keys_out.data_ptr(), keys_in.numel(),
+                                        int(bool(ascending)), _stream_handle(stream)), "bitonic_sort_u32_host")
+    return keys_out
+
+
+def sort_host_batch(keys_in, keys_out=None, ascending: bool = True, stream=None):
+    """Sorts a list of host tensors of 32-bit keys (page-locked for
+    asynchronous copies) into keys_out (default: in place), overlapping each
+    array's copies with its neighbours' passes.  Synchronise the stream
+    before reading keys_out."""
+    if keys_out is None:
+        keys_out = keys_in
+    if len(keys_in) != len(keys_out):
+        raise ValueError("keys_in and keys_out differ in length")
+    for a, b in zip(keys_in, keys_out):
+        for t in (a, b):
+            if t.is_cuda or t.element_size() != 4 or not t.is_contiguous():
+                raise ValueError("every array must be a contiguous host tensor of 4-byte keys")
+        if a.numel() != b.numel():
+            raise ValueError("an input and its output differ in length")
+    k = len(keys_in)
+    ins = (ctypes.c_void_p * k)(*[t.data_ptr() for t in keys_in])
+    outs = (ctypes.c_void_p * k)(*[t.data_ptr() for t in keys_out])
+    ns = (ctypes.c_size_t * k)(*[t.numel() for t in keys_in])
+    _check(load().bitonic_sort_u32_host_batch(ins, outs, ns, k, int(bool(ascending)), _stream_handle(stream)),
+           "bitonic_sort_u32_host_batch")
+    return keys_out
 
 
 def sort_pairs_(keys, vals, ascending: bool = True, stream=None):

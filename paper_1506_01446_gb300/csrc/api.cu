@@ -30,6 +30,9 @@ constexpr int kDevTimeout = 2;
 
 constexpr size_t kMaxGraphs = 64;
 constexpr uint64_t kMaxKeys = uint64_t(1) << 31;
+// Host-buffer sorts upload, tile-sort, final-pass and download in this many
+// chunks, so that copies overlap the passes that need only their own tiles.
+constexpr int kHostChunks = 8;
 
 std::mutex g_mu;  // guards every piece of state below
 Options g_opt;
@@ -41,6 +44,17 @@ struct StreamWs {
     size_t comp_cap = 0;         // in elements
     void* seg = nullptr;         // segmented batch plan, class bytes and class order
     size_t seg_cap = 0;          // in bytes
+    // host-buffer sorts: a second stream (uploads and downloads stay on the
+    // caller's stream, the tile passes run here) and chunk events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev[2 * kHostChunks + 1] = {};
+    // batched host-buffer sorts: upload and download streams, a second
+    // device buffer, and per-buffer chunk / free events
+    cudaStream_t up = nullptr, down = nullptr;
+    uint32_t* buf2 = nullptr;
+    size_t buf2_cap = 0;  // in keys
+    cudaEvent_t bev[2][2 * kHostChunks + 1] = {};
+    cudaEvent_t bstart = nullptr;
 };
 
 struct PlanEntry {
@@ -446,6 +460,237 @@ bitonic_status sort_keys_impl(void* keys, size_t n, int type, int ascending, cud
     });
 }
 
+// Tile launch i of a plan restricted to its tiles [t0, t1) (non-pipelined).
+cudaError_t launch_plan_tiles(const DeviceState& ds, const PlanEntry& pe, size_t i, void* base, uint32_t lo,
+                              uint32_t hi, const KeyMapHost& mi, const KeyMapHost& mo, cudaStream_t s, uint32_t t0,
+                              uint32_t t1)
+{
+    const Plan& pl = pe.plan;
+    const Launch& L = pl.launches[i];
+    const TileParams* hP = L.small ? &pl.small[L.desc] : nullptr;
+    const TileParamsBig* dP = L.small ? nullptr : pe.d_descs + L.desc;
+    const uint32_t pf = pe.opt.l2_prefetch > 0
+                            ? (uint32_t)(pe.opt.l2_prefetch * ds.tile_blocks[pl.cfg] * ds.num_sms)
+                            : 0u;
+    return launch_tile(pl.cfg, base, lo, hi, hP, dP, t1 - t0, mi, mo, s, pf, t0);
+}
+
+// Host-buffer sort of one array through the device buffer `dev`, for a plan
+// whose first launch is a tile sort on contiguous tiles: the upload runs in
+// chunks on `up`, each chunk's tiles are sorted on `comp` once they arrive,
+// the other launches follow on `comp`, and the download runs on `down`, chunk
+// by chunk as the last launch finishes them when it also works on
+// contiguous tiles.  ev_in / ev_out: kHostChunks events each.  The caller
+// orders `comp` and `down` after earlier work (the streams wait on events).
+bitonic_status enqueue_host_sort(const DeviceState& ds, const PlanEntry& pe, const uint32_t* in, uint32_t* out,
+                                 size_t n, const KeyMaps& km, uint32_t* dev, cudaStream_t up, cudaStream_t comp,
+                                 cudaStream_t down, cudaEvent_t* ev_in, cudaEvent_t* ev_out)
+{
+    const Plan& pl = pe.plan;
+    const size_t L = pl.launches.size();
+    const TileParamsBig& first = pl.descs[pl.launches[0].desc];
+    const bool last_tiled = pl.descs[pl.launches[L - 1].desc].contiguous;
+    const int m = first.m;
+    const uint32_t live = (uint32_t)((n + (size_t(1) << m) - 1) >> m);  // tiles holding real keys
+    const uint32_t nch = live < (uint32_t)kHostChunks ? live : (uint32_t)kHostChunks;
+    auto chunk_tiles = [&](uint32_t c) { return (uint32_t)((uint64_t)live * c / nch); };
+    auto chunk_keys = [&](uint32_t t) { return std::min<size_t>((size_t)t << m, n); };
+    const KeyMapHost ident;
+    // upload in chunks; the tile sort (launch 0) follows each chunk
+    for (uint32_t c = 0; c < nch; ++c) {
+        const size_t a = chunk_keys(chunk_tiles(c)), b = chunk_keys(chunk_tiles(c + 1));
+        BT_CK(cudaMemcpyAsync(dev + a, in + a, (b - a) * sizeof(uint32_t), cudaMemcpyHostToDevice, up));
+        BT_CK(cudaEventRecord(ev_in[c], up));
+        BT_CK(cudaStreamWaitEvent(comp, ev_in[c], 0));
+        const bool also_last = L == 1;
+        cudaError_t e = launch_plan_tiles(ds, pe, 0, dev, 0, (uint32_t)n, km.in, also_last ? km.out : ident, comp,
+                                          chunk_tiles(c), chunk_tiles(c + 1));
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        if (also_last) BT_CK(cudaEventRecord(ev_out[c], comp));
+    }
+    if (L > 1) {
+        // the middle launches over all tiles, then the last launch
+        for (size_t i = 1; i + 1 < L; ++i) {
+            const Launch& Li = pl.launches[i];
+            const TileParamsBig& D = pl.descs[Li.desc];
+            uint32_t ntiles = Li.grid;
+            if (D.contiguous) ntiles = std::min<uint32_t>(ntiles, (uint32_t)((n + (size_t(1) << D.m) - 1) >> D.m));
+            cudaError_t e = launch_plan_tiles(ds, pe, i, dev, 0, (uint32_t)n, ident, ident, comp, 0, ntiles);
+            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        }
+        if (last_tiled) {
+            for (uint32_t c = 0; c < nch; ++c) {
+                cudaError_t e = launch_plan_tiles(ds, pe, L - 1, dev, 0, (uint32_t)n, ident, km.out, comp,
+                                                  chunk_tiles(c), chunk_tiles(c + 1));
+                if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+                BT_CK(cudaEventRecord(ev_out[c], comp));
+            }
+        } else {
+            const Launch& Ll = pl.launches[L - 1];
+            cudaError_t e = launch_plan_tiles(ds, pe, L - 1, dev, 0, (uint32_t)n, ident, km.out, comp, 0, Ll.grid);
+            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+            for (uint32_t c = 0; c < nch; ++c) BT_CK(cudaEventRecord(ev_out[c], comp));
+        }
+    }
+    // download each chunk once its last launch is done
+    for (uint32_t c = 0; c < nch; ++c) {
+        const size_t a = chunk_keys(chunk_tiles(c)), b = chunk_keys(chunk_tiles(c + 1));
+        BT_CK(cudaStreamWaitEvent(down, ev_out[c], 0));
+        BT_CK(cudaMemcpyAsync(out + a, dev + a, (b - a) * sizeof(uint32_t), cudaMemcpyDeviceToHost, down));
+    }
+    return BITONIC_OK;
+}
+
+// 4-byte keys from host memory: in[0..n) -> out[0..n) (in may equal out).
+// The keys go through a per-stream device buffer.  When the plan starts with
+// a tile sort on contiguous tiles (every plan of the optimized and semi
+// variants), the upload runs in chunks on the caller's stream and each
+// chunk's tiles are sorted on a second stream as soon as they arrive; when
+// the last launch also works on contiguous tiles, its chunks are downloaded
+// as each finishes.  Otherwise upload, sort and download run in turn.
+bitonic_status sort_u32_host_impl(const uint32_t* in, uint32_t* out, size_t n, int ascending, cudaStream_t s)
+{
+    if (n > kMaxKeys) return BITONIC_ERR_UNSUPPORTED;
+    if (n == 0) return BITONIC_OK;
+    if (!in || !out) {
+        t_last_error = "null host pointer";
+        return BITONIC_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> g(g_mu);
+    bitonic_status st;
+    if (stream_capturing(s)) {
+        t_last_error = "host-buffer sorts are not captured into graphs";
+        return BITONIC_ERR_UNSUPPORTED;
+    }
+    DeviceState* ds;
+    if ((st = device_state(&ds))) return st;
+    StreamWs* w;
+    if ((st = stream_ws(*ds, s, (n + 1) / 2, &w))) return st;
+    if (!w->side) {
+        BT_CK(cudaStreamCreateWithFlags(&w->side, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : w->ev) BT_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    uint32_t* dev = reinterpret_cast<uint32_t*>(w->comp);
+    const size_t bytes = n * sizeof(uint32_t);
+    if (n == 1) {
+        BT_CK(cudaMemcpyAsync(dev, in, bytes, cudaMemcpyHostToDevice, s));
+        BT_CK(cudaMemcpyAsync(out, dev, bytes, cudaMemcpyDeviceToHost, s));
+        return BITONIC_OK;
+    }
+    PlanEntry* pe;
+    if ((st = get_plan(*ds, n, 4, &pe))) return st;
+    const Plan& pl = pe->plan;
+    const KeyMaps km = key_maps(KEY_U32, ascending);
+    const bool tiles = !pl.launches.empty() && pl.launches[0].kind != KIND_STEP && !pe->opt.pipeline &&
+                       pl.descs[pl.launches[0].desc].contiguous;
+    if (!tiles) {
+        BT_CK(cudaMemcpyAsync(dev, in, bytes, cudaMemcpyHostToDevice, s));
+        if ((st = enqueue_plan(*ds, *pe, dev, 0, (uint32_t)n, km, 4, ds->status, s, nullptr, nullptr))) return st;
+        BT_CK(cudaMemcpyAsync(out, dev, bytes, cudaMemcpyDeviceToHost, s));
+        return BITONIC_OK;
+    }
+    BT_CK(cudaEventRecord(w->ev[2 * kHostChunks], s));
+    BT_CK(cudaStreamWaitEvent(w->side, w->ev[2 * kHostChunks], 0));
+    return enqueue_host_sort(*ds, *pe, in, out, n, km, dev, s, w->side, s, w->ev, w->ev + kHostChunks);
+}
+
+// Batched host-buffer sorts: arrays j = 0..count-1 alternate between two
+// device buffers.  Uploads run on one stream, the passes on a second (one
+// array after another), downloads on a third, so that array j+1's upload
+// and array j-1's download overlap array j's passes.  A buffer is refilled
+// only after its previous download has finished.  Plans that cannot take
+// chunked tile launches run the arrays one after another on `s`.
+bitonic_status sort_u32_host_batch_impl(const uint32_t* const* in, uint32_t* const* out, const size_t* n, int count,
+                                        int ascending, cudaStream_t s)
+{
+    if (count < 0 || (count > 0 && (!in || !out || !n))) {
+        t_last_error = "bad batch arrays";
+        return BITONIC_ERR_INVALID;
+    }
+    size_t maxn = 0;
+    for (int j = 0; j < count; ++j) {
+        if (n[j] > kMaxKeys) return BITONIC_ERR_UNSUPPORTED;
+        if (n[j] && (!in[j] || !out[j])) {
+            t_last_error = "null host pointer";
+            return BITONIC_ERR_INVALID;
+        }
+        maxn = std::max(maxn, n[j]);
+    }
+    if (maxn == 0) return BITONIC_OK;
+    bitonic_status st;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        if (stream_capturing(s)) {
+            t_last_error = "host-buffer sorts are not captured into graphs";
+            return BITONIC_ERR_UNSUPPORTED;
+        }
+        DeviceState* ds;
+        if ((st = device_state(&ds))) return st;
+        StreamWs* w;
+        if ((st = stream_ws(*ds, s, (maxn + 1) / 2, &w))) return st;
+        if (!w->up) {
+            if (!w->side) {
+                BT_CK(cudaStreamCreateWithFlags(&w->side, cudaStreamNonBlocking));
+                for (cudaEvent_t& e : w->ev) BT_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            }
+            BT_CK(cudaStreamCreateWithFlags(&w->up, cudaStreamNonBlocking));
+            BT_CK(cudaStreamCreateWithFlags(&w->down, cudaStreamNonBlocking));
+            for (auto& row : w->bev)
+                for (cudaEvent_t& e : row) BT_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            BT_CK(cudaEventCreateWithFlags(&w->bstart, cudaEventDisableTiming));
+        }
+        if (maxn > w->buf2_cap) {
+            if (w->buf2) {
+                BT_CK(cudaStreamSynchronize(s));
+                BT_CK(cudaFree(w->buf2));
+                w->buf2 = nullptr;
+                w->buf2_cap = 0;
+            }
+            BT_CK(cudaMalloc(&w->buf2, maxn * sizeof(uint32_t)));
+            w->buf2_cap = maxn;
+        }
+        uint32_t* bufs[2] = {reinterpret_cast<uint32_t*>(w->comp), w->buf2};
+        const KeyMaps km = key_maps(KEY_U32, ascending);
+        BT_CK(cudaEventRecord(w->bstart, s));
+        for (cudaStream_t t : {w->up, w->side, w->down}) BT_CK(cudaStreamWaitEvent(t, w->bstart, 0));
+        for (int j = 0; j < count; ++j) {
+            if (n[j] == 0) continue;
+            const int b = j & 1;
+            uint32_t* dev = bufs[b];
+            cudaEvent_t* ev_in = w->bev[b];
+            cudaEvent_t* ev_out = w->bev[b] + kHostChunks;
+            cudaEvent_t ev_free = w->bev[b][2 * kHostChunks];
+            if (j >= 2) BT_CK(cudaStreamWaitEvent(w->up, ev_free, 0));  // buffer b's last download is done
+            const size_t bytes = n[j] * sizeof(uint32_t);
+            PlanEntry* pe = nullptr;
+            if (n[j] > 1 && (st = get_plan(*ds, n[j], 4, &pe))) return st;
+            const bool tiles = pe && pe->plan.launches[0].kind != KIND_STEP && !pe->opt.pipeline &&
+                               pe->plan.descs[pe->plan.launches[0].desc].contiguous;
+            if (tiles) {
+                if ((st = enqueue_host_sort(*ds, *pe, in[j], out[j], n[j], km, dev, w->up, w->side, w->down, ev_in,
+                                            ev_out)))
+                    return st;
+            } else {
+                // upload, sort and download in turn, ordered through the three streams
+                BT_CK(cudaMemcpyAsync(dev, in[j], bytes, cudaMemcpyHostToDevice, w->up));
+                BT_CK(cudaEventRecord(ev_in[0], w->up));
+                BT_CK(cudaStreamWaitEvent(w->side, ev_in[0], 0));
+                if (pe && (st = enqueue_plan(*ds, *pe, dev, 0, (uint32_t)n[j], km, 4, ds->status, w->side, nullptr,
+                                             nullptr)))
+                    return st;
+                BT_CK(cudaEventRecord(ev_out[0], w->side));
+                BT_CK(cudaStreamWaitEvent(w->down, ev_out[0], 0));
+                BT_CK(cudaMemcpyAsync(out[j], dev, bytes, cudaMemcpyDeviceToHost, w->down));
+            }
+            BT_CK(cudaEventRecord(ev_free, w->down));
+        }
+        // the caller's stream continues once every download (hence every pass) is done
+        BT_CK(cudaEventRecord(w->bstart, w->down));
+        BT_CK(cudaStreamWaitEvent(s, w->bstart, 0));
+    }
+    return BITONIC_OK;
+}
+
 bitonic_status sort_pairs_impl(uint32_t* keys, uint32_t* vals, size_t n, int ascending, cudaStream_t s)
 {
     if (n > kMaxKeys) return BITONIC_ERR_UNSUPPORTED;
@@ -547,6 +792,18 @@ extern "C" {
 bitonic_status bitonic_sort_u32(uint32_t* keys, size_t n, int ascending, bitonic_stream_t stream)
 {
     return sort_keys_impl(keys, n, KEY_U32, ascending, (cudaStream_t)stream, nullptr, 0, nullptr);
+}
+
+bitonic_status bitonic_sort_u32_host(const uint32_t* in, uint32_t* out, size_t n, int ascending,
+                                     bitonic_stream_t stream)
+{
+    return sort_u32_host_impl(in, out, n, ascending, (cudaStream_t)stream);
+}
+
+bitonic_status bitonic_sort_u32_host_batch(const uint32_t* const* in, uint32_t* const* out, const size_t* n,
+                                           int count, int ascending, bitonic_stream_t stream)
+{
+    return sort_u32_host_batch_impl(in, out, n, count, ascending, (cudaStream_t)stream);
 }
 
 bitonic_status bitonic_sort_i32(int32_t* keys, size_t n, int ascending, bitonic_stream_t stream)
@@ -653,6 +910,16 @@ bitonic_status bitonic_release_workspace(void)
         if (kv.second.host) cudaFreeHost(kv.second.host);
         if (kv.second.comp) cudaFree(kv.second.comp);
         if (kv.second.seg) cudaFree(kv.second.seg);
+        for (cudaEvent_t e : kv.second.ev)
+            if (e) cudaEventDestroy(e);
+        if (kv.second.side) cudaStreamDestroy(kv.second.side);
+        for (auto& row : kv.second.bev)
+            for (cudaEvent_t e : row)
+                if (e) cudaEventDestroy(e);
+        if (kv.second.bstart) cudaEventDestroy(kv.second.bstart);
+        if (kv.second.up) cudaStreamDestroy(kv.second.up);
+        if (kv.second.down) cudaStreamDestroy(kv.second.down);
+        if (kv.second.buf2) cudaFree(kv.second.buf2);
     }
     ds.ws.clear();
     return BITONIC_OK;

@@ -47,16 +47,17 @@ struct KeyMapHost {
     uint64_t a = 0, b = 0, s = 0;
 };
 
-// Tile launches; real keys pass through mi on load and mo on store.
+// Tile launches; real keys pass through mi on load and mo on store.  CTA i
+// of the launch runs tile cta0 + i of the pass (a launch may cover a range).
 cudaError_t launch_tile(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
                         const TileParamsBig* dP, uint32_t grid, const KeyMapHost& mi, const KeyMapHost& mo,
-                        cudaStream_t s, uint32_t pf_dist = 0);
+                        cudaStream_t s, uint32_t pf_dist = 0, uint32_t cta0 = 0);
 cudaError_t launch_tile_u32(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
                             const TileParamsBig* dP, uint32_t grid, const KeyMapHost& mi, const KeyMapHost& mo,
-                            uint32_t pf_dist, cudaStream_t s);
+                            uint32_t pf_dist, uint32_t cta0, cudaStream_t s);
 cudaError_t launch_tile_u64(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
                             const TileParamsBig* dP, uint32_t grid, const KeyMapHost& mi, const KeyMapHost& mo,
-                            uint32_t pf_dist, cudaStream_t s);
+                            uint32_t pf_dist, uint32_t cta0, cudaStream_t s);
 // Applies a key map to base[lo, hi) in one elementwise pass (for launch
 // kinds that cannot fuse it: the one-step kernels, the pipelined kernels
 // with a float map).

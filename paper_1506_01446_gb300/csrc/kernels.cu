@@ -75,10 +75,11 @@ cudaError_t launch_step_t(K* base, uint32_t lo, uint32_t hi, uint32_t N, int j, 
 
 cudaError_t launch_tile(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
                         const TileParamsBig* dP, uint32_t grid, const KeyMapHost& mi, const KeyMapHost& mo,
-                        cudaStream_t s, uint32_t pf_dist)
+                        cudaStream_t s, uint32_t pf_dist, uint32_t cta0)
 {
-    if (tile_cfg(cfg).key_bytes == 4) return launch_tile_u32(cfg, base, lo, hi, hP, dP, grid, mi, mo, pf_dist, s);
-    return launch_tile_u64(cfg, base, lo, hi, hP, dP, grid, mi, mo, pf_dist, s);
+    if (tile_cfg(cfg).key_bytes == 4)
+        return launch_tile_u32(cfg, base, lo, hi, hP, dP, grid, mi, mo, pf_dist, cta0, s);
+    return launch_tile_u64(cfg, base, lo, hi, hP, dP, grid, mi, mo, pf_dist, cta0, s);
 }
 
 // One elementwise pass of a key map over base[lo, hi).

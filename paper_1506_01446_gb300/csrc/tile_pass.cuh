@@ -95,13 +95,15 @@ __device__ __forceinline__ void run_tile_rounds(Tile<K, DESC, LOG_R, LOG_T>& t,
 // rounds (register network steps, shared-memory transposes in between), store.
 // Prefetches into L2 the rows of the tile `dist` CTAs ahead (the one a CTA
 // starting about one resident wave later will load), with TMA bulk
-// prefetches: no registers or shared memory are spent on it.
+// prefetches: no registers or shared memory are spent on it.  Tiles are
+// numbered from cta0 (a launch may cover a range of a pass's tiles).
 template <typename K, int LOG_T, class PT>
-__device__ __forceinline__ void prefetch_tile_l2(const K* base, uint32_t lo, uint32_t hi, const PT& P, uint32_t dist)
+__device__ __forceinline__ void prefetch_tile_l2(const K* base, uint32_t lo, uint32_t hi, const PT& P, uint32_t dist,
+                                                 uint32_t cta0)
 {
     const uint32_t t = blockIdx.x + dist;
     if (!dist || t >= gridDim.x) return;
-    const uint32_t g0 = cta_base(P, t);
+    const uint32_t g0 = cta_base(P, cta0 + t);
     const int c = P.row_log;
     const uint32_t row_len = 1u << c;
     const uint32_t nrows = 1u << (P.m - c);
@@ -120,13 +122,13 @@ __device__ __forceinline__ void prefetch_tile_l2(const K* base, uint32_t lo, uin
 
 template <typename K, bool DESC, int LOG_R, int LOG_T, bool CATALOG, class PT>
 __device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uint32_t hi, const PT& P,
-                                          KeyMap<K> m_in, KeyMap<K> m_out, uint32_t pf_dist = 0)
+                                          KeyMap<K> m_in, KeyMap<K> m_out, uint32_t pf_dist = 0, uint32_t cta0 = 0)
 {
     using T = Tile<K, DESC, LOG_R, LOG_T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto* sm = reinterpret_cast<typename T::Vec*>(smem_raw);
     const uint32_t x = threadIdx.x;
-    const uint32_t g0 = cta_base(P, blockIdx.x);
+    const uint32_t g0 = cta_base(P, cta0 + blockIdx.x);
     if (P.contiguous && g0 >= hi) return;  // the whole tile is tail padding
     const bool interior = (g0 & ~P.span_mask) >= lo && (g0 | P.span_mask) < hi;
     T t;
@@ -134,7 +136,7 @@ __device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uin
         t.load_global_interior(base, P.io[0], g0, x, m_in);
     else
         t.load_global(base, lo, hi, P.io[0], g0, x, m_in);
-    prefetch_tile_l2<K, LOG_T>(base, lo, hi, P, pf_dist);
+    prefetch_tile_l2<K, LOG_T>(base, lo, hi, P, pf_dist, cta0);
     run_tile_rounds<K, DESC, LOG_R, LOG_T, CATALOG>(t, sm, P, x);
     if (interior)
         t.store_global_interior(base, P.io[1], g0, x, m_out);
@@ -149,36 +151,37 @@ __device__ __forceinline__ void tile_pass(K* __restrict__ base, uint32_t lo, uin
 // catalog (straight-line code per round shape) pays for its instruction
 // footprint with 4-byte keys (2^28: 13.5 vs 14.7 ms on GB300) but not with
 // 8-byte composites (2^26 pairs: 10.33 vs 10.22 ms), which use per-step
-// dispatch.
+// dispatch.  CTA i of the launch runs tile cta0 + i of the pass.
 template <typename K, int LOG_R, int LOG_T, int MINB>
 __global__ void __launch_bounds__(1 << LOG_T, MINB)
 k_tile(K* __restrict__ base, uint32_t lo, uint32_t hi, const __grid_constant__ TileParams P, KeyMap<K> m_in,
-       KeyMap<K> m_out, uint32_t pf_dist)
+       KeyMap<K> m_out, uint32_t pf_dist, uint32_t cta0)
 {
-    tile_pass<K, false, LOG_R, LOG_T, sizeof(K) == 4>(base, lo, hi, P, m_in, m_out, pf_dist);
+    tile_pass<K, false, LOG_R, LOG_T, sizeof(K) == 4>(base, lo, hi, P, m_in, m_out, pf_dist, cta0);
 }
 
 // Descriptor with more rounds than fit by value, read from global memory.
 template <typename K, int LOG_R, int LOG_T, int MINB>
 __global__ void __launch_bounds__(1 << LOG_T, MINB)
 k_tile_big(K* __restrict__ base, uint32_t lo, uint32_t hi, const TileParamsBig* __restrict__ P, KeyMap<K> m_in,
-           KeyMap<K> m_out)
+           KeyMap<K> m_out, uint32_t cta0)
 {
-    tile_pass<K, false, LOG_R, LOG_T, false>(base, lo, hi, *P, m_in, m_out);
+    tile_pass<K, false, LOG_R, LOG_T, false>(base, lo, hi, *P, m_in, m_out, 0, cta0);
 }
 
 // Launcher and attribute setup of one configuration.
 template <typename K, int LR, int LT, int MB>
 cudaError_t launch_tile_t(void* base, uint32_t lo, uint32_t hi, const TileParams* hP, const TileParamsBig* dP,
-                          uint32_t grid, const KeyMapHost& mi, const KeyMapHost& mo, uint32_t pf_dist, cudaStream_t s)
+                          uint32_t grid, const KeyMapHost& mi, const KeyMapHost& mo, uint32_t pf_dist, uint32_t cta0,
+                          cudaStream_t s)
 {
     constexpr int kThreads = 1 << LT;
     constexpr size_t kSmem = (size_t(1) << (LR + LT)) * sizeof(K);
     const KeyMap<K> ki{(K)mi.a, (K)mi.b, (K)mi.s}, ko{(K)mo.a, (K)mo.b, (K)mo.s};
     if (hP)
-        k_tile<K, LR, LT, MB><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, *hP, ki, ko, pf_dist);
+        k_tile<K, LR, LT, MB><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, *hP, ki, ko, pf_dist, cta0);
     else
-        k_tile_big<K, LR, LT, MB><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, dP, ki, ko);
+        k_tile_big<K, LR, LT, MB><<<grid, kThreads, kSmem, s>>>((K*)base, lo, hi, dP, ki, ko, cta0);
     return cudaGetLastError();
 }
 

@@ -6,10 +6,10 @@ namespace bitonic {
 
 cudaError_t launch_tile_u64(int cfg, void* base, uint32_t lo, uint32_t hi, const TileParams* hP,
                             const TileParamsBig* dP, uint32_t grid, const KeyMapHost& mi, const KeyMapHost& mo,
-                            uint32_t pf_dist, cudaStream_t s)
+                            uint32_t pf_dist, uint32_t cta0, cudaStream_t s)
 {
 #define BITONIC_CASE(ID, KT, LR, LT, MB) \
-    case ID: return launch_tile_t<KT, LR, LT, MB>(base, lo, hi, hP, dP, grid, mi, mo, pf_dist, s);
+    case ID: return launch_tile_t<KT, LR, LT, MB>(base, lo, hi, hP, dP, grid, mi, mo, pf_dist, cta0, s);
     switch (cfg) {
         BITONIC_TILE_CONFIGS_U64(BITONIC_CASE)
         default: return cudaErrorInvalidValue;

@@ -46,6 +46,16 @@ def test_argument_errors_need_no_gpu():
     assert lib.bitonic_sort_segmented_u32(16, 16, 0, None) == bt.OK
     assert lib.bitonic_sort_segmented_pairs_u32(16, None, 16, 3, None) == bt.ERR_INVALID
     assert lib.bitonic_sort_u32_profiled(16, 100, 1, None, None, 0, None) == bt.ERR_INVALID
+    assert lib.bitonic_sort_u32_host(None, None, 0, 1, None) == bt.OK
+    assert lib.bitonic_sort_u32_host(None, 16, 10, 1, None) == bt.ERR_INVALID
+    assert lib.bitonic_sort_u32_host(16, None, 10, 1, None) == bt.ERR_INVALID
+    assert lib.bitonic_sort_u32_host(16, 16, (1 << 31) + 1, 1, None) == bt.ERR_UNSUPPORTED
+    assert lib.bitonic_sort_u32_host_batch(None, None, None, 0, 1, None) == bt.OK
+    assert lib.bitonic_sort_u32_host_batch(None, None, None, -1, 1, None) == bt.ERR_INVALID
+    assert lib.bitonic_sort_u32_host_batch(None, None, None, 2, 1, None) == bt.ERR_INVALID
+    ptrs = (ctypes.c_void_p * 2)(16, None)
+    ns = (ctypes.c_size_t * 2)(10, 10)
+    assert lib.bitonic_sort_u32_host_batch(ptrs, ptrs, ns, 2, 1, None) == bt.ERR_INVALID
     for name, size in (("bitonic_sort_i32", 4), ("bitonic_sort_f32", 4), ("bitonic_sort_u64", 8),
                        ("bitonic_sort_i64", 8), ("bitonic_sort_f64", 8)):
         f = getattr(lib, name)

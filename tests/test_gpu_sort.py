@@ -327,3 +327,72 @@ def test_typed_keys_other_variants(kind, variant, pipeline):
         keys = workloads.typed_keys(kind, n, seed=n + 11)
         check_typed(keys, True)
         check_typed(keys, False)
+
+
+def host_tensor(a: np.ndarray, pinned=True):
+    t = torch.from_numpy(a.view(np.int32).copy())
+    return t.pin_memory() if pinned else t
+
+
+@pytest.mark.parametrize("ascending", [True, False])
+def test_host_buffer_sort(ascending):
+    # Sizes: one tile (a single launch), a partial last chunk, several
+    # chunks of a multi-pass plan, and 2^22 keys.
+    for n in [1, 2, 1000, 16384, 16385, 100003, (1 << 20) + 3, 1 << 22]:
+        keys = workloads.uniform_u32(n, seed=n + 5)
+        src, dst = host_tensor(keys), host_tensor(np.zeros(n, np.uint32))
+        bt.sort_host(src, dst, ascending)
+        torch.cuda.synchronize()
+        assert np.array_equal(dst.numpy().view(np.uint32), oracle.merge_sort(keys, ascending)), n
+        assert np.array_equal(src.numpy().view(np.uint32), keys)   # the input is left alone
+
+
+def test_host_buffer_sort_in_place_pageable_and_basic_variant():
+    keys = workloads.uniform_u32(300_001, seed=8)
+    t = host_tensor(keys)
+    bt.sort_host(t)                                  # in == out
+    torch.cuda.synchronize()
+    assert np.array_equal(t.numpy().view(np.uint32), oracle.merge_sort(keys))
+    p = host_tensor(keys, pinned=False)              # pageable memory
+    bt.sort_host(p, ascending=False)
+    torch.cuda.synchronize()
+    assert np.array_equal(p.numpy().view(np.uint32), oracle.merge_sort(keys, False))
+    bt.set_options(variant=1)                        # one-step kernels: upload, sort, download in turn
+    q = host_tensor(keys[:5000])
+    bt.sort_host(q)
+    torch.cuda.synchronize()
+    assert np.array_equal(q.numpy().view(np.uint32), oracle.merge_sort(keys[:5000]))
+
+
+def test_host_buffer_sorts_on_two_streams_overlap_correctly():
+    # Two calls in flight on different streams, each with its own device buffer.
+    a_keys, b_keys = workloads.uniform_u32(1 << 21, seed=1), workloads.uniform_u32((1 << 21) - 7, seed=2)
+    a_in, b_in = host_tensor(a_keys), host_tensor(b_keys)
+    a_out, b_out = host_tensor(np.zeros_like(a_keys)), host_tensor(np.zeros_like(b_keys))
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    for _ in range(2):
+        bt.sort_host(a_in, a_out, True, stream=s1)
+        bt.sort_host(b_in, b_out, False, stream=s2)
+    torch.cuda.synchronize()
+    assert np.array_equal(a_out.numpy().view(np.uint32), oracle.merge_sort(a_keys))
+    assert np.array_equal(b_out.numpy().view(np.uint32), oracle.merge_sort(b_keys, False))
+
+
+@pytest.mark.parametrize("ascending", [True, False])
+def test_host_buffer_batch(ascending):
+    # Mixed sizes (empty, one key, one tile, several chunks), in place and
+    # not, and an output buffer reused by arrays two apart (the later wins).
+    sizes = [0, 1, 5, 16384, 100003, (1 << 20) + 7, 1 << 21, 3000]
+    keys = [workloads.uniform_u32(n, seed=100 + i) for i, n in enumerate(sizes)]
+    ins = [host_tensor(k) for k in keys]
+    outs = [host_tensor(np.zeros(n, np.uint32)) if i % 3 else ins[i] for i, n in enumerate(sizes)]
+    bt.sort_host_batch(ins, outs, ascending)
+    torch.cuda.synchronize()
+    for i, k in enumerate(keys):
+        assert np.array_equal(outs[i].numpy().view(np.uint32), oracle.merge_sort(k, ascending)), sizes[i]
+    shared = host_tensor(np.zeros(1 << 20, np.uint32))
+    a, b = workloads.uniform_u32(1 << 20, seed=7), workloads.uniform_u32(1 << 20, seed=8)
+    bt.sort_host_batch([host_tensor(a), host_tensor(np.zeros(3, np.uint32)), host_tensor(b)],
+                       [shared, host_tensor(np.zeros(3, np.uint32)), shared], ascending)
+    torch.cuda.synchronize()
+    assert np.array_equal(shared.numpy().view(np.uint32), oracle.merge_sort(b, ascending))
