@@ -14,6 +14,7 @@
 
 #include "engine.cuh"
 #include "seg.h"
+#include "tile_pass.cuh"
 
 namespace bitonic {
 
@@ -135,14 +136,17 @@ k_seg_tiles(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const int3
                 }
             }
         }
-        run_round_steps<false>(tl.r, r0);
+        // straight-line round code from the catalog for 4-byte keys (as in the
+        // tile passes), per-step dispatch for composites
+        constexpr int kCat = sizeof(K) == 4 ? LOG_R : 0;
+        steps_in_place<kCat, false>(tl.r, r0);
         const int nr = P.nrounds;
         for (int rd = 1; rd < nr; ++rd) {
             if (rd > 1) __syncthreads();
             tl.smem_write(sm, P.rounds[rd - 1], x);
             __syncthreads();
             tl.smem_read(sm, P.rounds[rd], x);
-            run_round_steps<false>(tl.r, P.rounds[rd]);
+            steps_in_place<kCat, false>(tl.r, P.rounds[rd]);
         }
         // Store in the last round's layout.
         {
