@@ -737,7 +737,8 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
     StreamWs* w;
     const size_t seg_need = seg_tiles_ws_bytes(nseg);
     if ((st = stream_ws(*ds, s, 0, &w, seg_need))) return st;
-    const int tile_grid = 2 * ds->num_sms;   // two resident tile CTAs per SM
+    // persistent packed-tile CTAs: as many as are resident
+    const int tile_grid = (vals ? kSegTileBlocksPairs : kSegTileBlocksKeys) * ds->num_sms;
     const int large_grid = 4 * ds->num_sms;
     if (!vals) {
         GraphKey key{2, 0, 1, (uintptr_t)keys, 0, (uintptr_t)offsets, nseg, (uintptr_t)s, 0, 0, 0};

@@ -12,6 +12,12 @@ constexpr int kSegClasses = 32;       // size classes: k = ceil(log2 length)
 constexpr int kSegClassSkip = 30;     // length 0 or 1: nothing to do
 constexpr int kSegClassLarge = 31;    // longer than one tile
 constexpr int kSegMaxPerTile = 1024;  // segments packed into one tile at most
+// Resident CTAs per SM of the packed-tile kernels (registers bounded for it;
+// the persistent grid is this many CTAs per SM): 4-byte keys, composites.
+// Three for 4-byte keys (80 registers, a few spills) measured 0.78 ms against
+// 0.77 ms with two for 65,536 arrays of up to 8192 keys.
+constexpr int kSegTileBlocksKeys = 2;
+constexpr int kSegTileBlocksPairs = 2;
 
 // Device-side plan of one segmented batch (built by the classify / scan kernels).
 struct SegPlan {

@@ -74,8 +74,8 @@ __global__ void k_seg_scatter(const uint8_t* __restrict__ cls, int nseg, SegPlan
 
 // Packed tile sort.  K = uint32_t (keys) or uint64_t (composite of key and
 // position in its segment, for pairs).
-template <typename K, int LOG_R, int LOG_T>
-__global__ void __launch_bounds__(1 << LOG_T)
+template <typename K, int LOG_R, int LOG_T, int MINB>
+__global__ void __launch_bounds__(1 << LOG_T, MINB)
 k_seg_tiles(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const int32_t* __restrict__ offs,
             const int32_t* __restrict__ order, const SegPlan* __restrict__ plan,
             const TileParamsBig* __restrict__ descs, int* counter)
@@ -210,11 +210,15 @@ constexpr size_t seg_tile_smem()
 
 cudaError_t seg_tiles_init_attributes()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_seg_tiles<uint32_t, 6, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_seg_tiles<uint32_t, 6, 8, kSegTileBlocksKeys>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)seg_tile_smem<uint32_t, 6, 8>());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_seg_tiles<uint64_t, 5, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)seg_tile_smem<uint64_t, 5, 8>());
+        e = cudaFuncSetAttribute(k_seg_tiles<uint32_t, 6, 8, kSegTileBlocksKeys>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_seg_tiles<uint64_t, 5, 8, kSegTileBlocksPairs>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_tile_smem<uint64_t, 5, 8>());
     return e;
 }
 
@@ -237,10 +241,10 @@ cudaError_t seg_tiles_launch(uint32_t* keys, uint32_t* vals, const int32_t* offs
     k_seg_scan<<<1, 32, 0, s>>>(plan, m);
     k_seg_scatter<<<cgrid, 256, 0, s>>>(cls, nseg, plan, order);
     if (pairs)
-        k_seg_tiles<uint64_t, 5, 8><<<grid, kSegTileThreads, seg_tile_smem<uint64_t, 5, 8>(), s>>>(
+        k_seg_tiles<uint64_t, 5, 8, kSegTileBlocksPairs><<<grid, kSegTileThreads, seg_tile_smem<uint64_t, 5, 8>(), s>>>(
             keys, vals, offs, order, plan, class_descs, &plan->tile_counter);
     else
-        k_seg_tiles<uint32_t, 6, 8><<<grid, kSegTileThreads, seg_tile_smem<uint32_t, 6, 8>(), s>>>(
+        k_seg_tiles<uint32_t, 6, 8, kSegTileBlocksKeys><<<grid, kSegTileThreads, seg_tile_smem<uint32_t, 6, 8>(), s>>>(
             keys, nullptr, offs, order, plan, class_descs, &plan->tile_counter);
     return cudaGetLastError();
 }
