@@ -58,6 +58,9 @@ static __constant__ uint32_t c_ce_mul[2] = {1u, 0xFFFFFFFFu};
 // Compare-exchange: the lower register receives the key that sorts first.
 // fma_hi: the multiply-add form (4-byte keys; exact modulo 2^32, since the
 // minimum is one of the two keys).  Constant once the caller's loop unrolls.
+// 8-byte keys take the larger key as a ^ b ^ min(a, b): one 64-bit compare
+// and two selects, then two logic ops instead of two more selects (9.0 vs
+// 6.9 compare-exchanges per clock per SM in a register-only probe).
 template <bool DESC, typename K>
 __device__ __forceinline__ void cmpx(K& a, K& b, bool fma_hi = false)
 {
@@ -66,6 +69,9 @@ __device__ __forceinline__ void cmpx(K& a, K& b, bool fma_hi = false)
         lo = a < b ? a : b;
         const K sum = a * c_ce_mul[0] + b;
         hi = lo * c_ce_mul[1] + sum;
+    } else if (sizeof(K) == 8) {
+        lo = a < b ? a : b;
+        hi = a ^ b ^ lo;
     } else {
         lo = a < b ? a : b;
         hi = a < b ? b : a;

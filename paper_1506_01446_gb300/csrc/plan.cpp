@@ -299,11 +299,12 @@ int choose_cfg(int key_bytes, const Options& opt)
     // the largest configured value below that.
     const int pref_r = opt.keys_per_thread_log2 ? opt.keys_per_thread_log2 : (key_bytes == 4 ? 6 : 5);
     // Register cap: 3 = kernels capped for three resident CTAs per SM, 2 =
-    // kernels bounded for two; 0 = automatic (three).  A cap is taken where
-    // a capped kernel of this shape exists; other shapes fall back to the
-    // two-CTA kernel.  (On GB300 at 2^26: 8-byte keys 8.8 ms capped against
-    // 11.9 ms two-CTA; 4-byte keys within 1-4% either way.)
-    const int cap = opt.ctas_per_sm ? opt.ctas_per_sm : 3;
+    // kernels bounded for two; 0 = automatic: three for 4-byte keys (4%
+    // faster at 2^24, within 1% at 2^28 on GB300), two for 8-byte keys (2^26
+    // uint64: 7.84 ms against 8.35 ms for the capped kernel, which spills).
+    // A cap is taken where a capped kernel of this shape exists; other shapes
+    // fall back to the two-CTA kernel.
+    const int cap = opt.ctas_per_sm ? opt.ctas_per_sm : (key_bytes == 4 ? 3 : 2);
     const int want_blocks = cap == 3 ? 3 : 1;
     for (int blocks : {want_blocks, 1}) {
         int best = -1;
