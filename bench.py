@@ -346,13 +346,15 @@ def run_reference(args, world, rank):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = n_sample * args.steps / total / 1e9
-    sample = f"{args.steps} x 2^20 uniform uint32 keys (bounded sample of the 2^28 workload)"
+    sample = f"{args.steps} x 2^20 uniform uint32 keys (bounded sample of the 2^{args.n_log2} workload)"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (splitmix64 uniform uint32)",
-        "config": {"workload": "uniform uint32 sort, CPU oracle sample", "n": n_sample},
+        # the arm's workload; each step times a bounded sample of it (cpu_baseline.sample)
+        "config": {"workload": f"single uint32 array, n=2^{args.n_log2}, uniform random, ascending",
+                   "n": 1 << args.n_log2, "parallelism": "replicas x1", "sample_keys_per_step": n_sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
