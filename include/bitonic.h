@@ -32,8 +32,9 @@
  *     N = next_pow2(n): positions >= n behave as keys that sort after every
  *     real key (0xFFFFFFFF ascending); they are never read or written.
  *   - The library owns a per-(device, stream) workspace (pair composites,
- *     work counters) that grows on demand with cudaMalloc and is freed by
- *     bitonic_release_workspace().  Keys-only sorts need none.  Calls on
+ *     work counters; the device buffers, streams and events of the
+ *     host-buffer sorts) that grows on demand with cudaMalloc and is freed by
+ *     bitonic_release_workspace().  Keys-only device sorts need none.  Calls on
  *     different streams may run concurrently from different host threads;
  *     calls on one stream are serialised by the caller.  While a stream is
  *     being captured nothing is allocated: a pair or segmented call then needs
