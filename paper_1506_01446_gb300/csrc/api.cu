@@ -476,15 +476,16 @@ cudaError_t launch_plan_tiles(const DeviceState& ds, const PlanEntry& pe, size_t
 }
 
 // Host-buffer sort of one array through the device buffer `dev`, for a plan
-// whose first launch is a tile sort on contiguous tiles: the upload runs in
-// chunks on `up`, each chunk's tiles are sorted on `comp` once they arrive,
-// the other launches follow on `comp`, and the download runs on `down`, chunk
-// by chunk as the last launch finishes them when it also works on
-// contiguous tiles.  ev_in / ev_out: kHostChunks events each.  The caller
-// orders `comp` and `down` after earlier work (the streams wait on events).
+// whose first launch is a tile sort on contiguous tiles.  The upload runs on
+// `up` in n_up chunks and each chunk's tiles are sorted on `comp` once they
+// arrive; the other launches follow on `comp`; the download runs on `down`
+// in n_down chunks, each as soon as the last launch has finished its tiles
+// (when that launch works on contiguous tiles; otherwise after it).  Chunk
+// counts are capped at kHostChunks and at the tile count; ev_in / ev_out hold
+// kHostChunks events each.  The caller orders the streams after earlier work.
 bitonic_status enqueue_host_sort(const DeviceState& ds, const PlanEntry& pe, const uint32_t* in, uint32_t* out,
                                  size_t n, const KeyMaps& km, uint32_t* dev, cudaStream_t up, cudaStream_t comp,
-                                 cudaStream_t down, cudaEvent_t* ev_in, cudaEvent_t* ev_out)
+                                 cudaStream_t down, cudaEvent_t* ev_in, cudaEvent_t* ev_out, int n_up, int n_down)
 {
     const Plan& pl = pe.plan;
     const size_t L = pl.launches.size();
@@ -492,19 +493,23 @@ bitonic_status enqueue_host_sort(const DeviceState& ds, const PlanEntry& pe, con
     const bool last_tiled = pl.descs[pl.launches[L - 1].desc].contiguous;
     const int m = first.m;
     const uint32_t live = (uint32_t)((n + (size_t(1) << m) - 1) >> m);  // tiles holding real keys
-    const uint32_t nch = live < (uint32_t)kHostChunks ? live : (uint32_t)kHostChunks;
-    auto chunk_tiles = [&](uint32_t c) { return (uint32_t)((uint64_t)live * c / nch); };
-    auto chunk_keys = [&](uint32_t t) { return std::min<size_t>((size_t)t << m, n); };
+    auto chunks = [&](int want) {
+        const uint32_t c = (uint32_t)std::max(1, std::min(want, kHostChunks));
+        return live < c ? live : c;
+    };
+    const uint32_t nin = chunks(n_up), nout = chunks(L == 1 ? n_up : n_down);
+    auto tiles_of = [&](uint32_t c, uint32_t nch) { return (uint32_t)((uint64_t)live * c / nch); };
+    auto keys_of = [&](uint32_t t) { return std::min<size_t>((size_t)t << m, n); };
     const KeyMapHost ident;
     // upload in chunks; the tile sort (launch 0) follows each chunk
-    for (uint32_t c = 0; c < nch; ++c) {
-        const size_t a = chunk_keys(chunk_tiles(c)), b = chunk_keys(chunk_tiles(c + 1));
+    for (uint32_t c = 0; c < nin; ++c) {
+        const size_t a = keys_of(tiles_of(c, nin)), b = keys_of(tiles_of(c + 1, nin));
         BT_CK(cudaMemcpyAsync(dev + a, in + a, (b - a) * sizeof(uint32_t), cudaMemcpyHostToDevice, up));
         BT_CK(cudaEventRecord(ev_in[c], up));
         BT_CK(cudaStreamWaitEvent(comp, ev_in[c], 0));
         const bool also_last = L == 1;
         cudaError_t e = launch_plan_tiles(ds, pe, 0, dev, 0, (uint32_t)n, km.in, also_last ? km.out : ident, comp,
-                                          chunk_tiles(c), chunk_tiles(c + 1));
+                                          tiles_of(c, nin), tiles_of(c + 1, nin));
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         if (also_last) BT_CK(cudaEventRecord(ev_out[c], comp));
     }
@@ -519,9 +524,9 @@ bitonic_status enqueue_host_sort(const DeviceState& ds, const PlanEntry& pe, con
             if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         }
         if (last_tiled) {
-            for (uint32_t c = 0; c < nch; ++c) {
+            for (uint32_t c = 0; c < nout; ++c) {
                 cudaError_t e = launch_plan_tiles(ds, pe, L - 1, dev, 0, (uint32_t)n, ident, km.out, comp,
-                                                  chunk_tiles(c), chunk_tiles(c + 1));
+                                                  tiles_of(c, nout), tiles_of(c + 1, nout));
                 if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
                 BT_CK(cudaEventRecord(ev_out[c], comp));
             }
@@ -529,12 +534,12 @@ bitonic_status enqueue_host_sort(const DeviceState& ds, const PlanEntry& pe, con
             const Launch& Ll = pl.launches[L - 1];
             cudaError_t e = launch_plan_tiles(ds, pe, L - 1, dev, 0, (uint32_t)n, ident, km.out, comp, 0, Ll.grid);
             if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-            for (uint32_t c = 0; c < nch; ++c) BT_CK(cudaEventRecord(ev_out[c], comp));
+            for (uint32_t c = 0; c < nout; ++c) BT_CK(cudaEventRecord(ev_out[c], comp));
         }
     }
     // download each chunk once its last launch is done
-    for (uint32_t c = 0; c < nch; ++c) {
-        const size_t a = chunk_keys(chunk_tiles(c)), b = chunk_keys(chunk_tiles(c + 1));
+    for (uint32_t c = 0; c < nout; ++c) {
+        const size_t a = keys_of(tiles_of(c, nout)), b = keys_of(tiles_of(c + 1, nout));
         BT_CK(cudaStreamWaitEvent(down, ev_out[c], 0));
         BT_CK(cudaMemcpyAsync(out + a, dev + a, (b - a) * sizeof(uint32_t), cudaMemcpyDeviceToHost, down));
     }
@@ -591,7 +596,8 @@ bitonic_status sort_u32_host_impl(const uint32_t* in, uint32_t* out, size_t n, i
     }
     BT_CK(cudaEventRecord(w->ev[2 * kHostChunks], s));
     BT_CK(cudaStreamWaitEvent(w->side, w->ev[2 * kHostChunks], 0));
-    return enqueue_host_sort(*ds, *pe, in, out, n, km, dev, s, w->side, s, w->ev, w->ev + kHostChunks);
+    return enqueue_host_sort(*ds, *pe, in, out, n, km, dev, s, w->side, s, w->ev, w->ev + kHostChunks, kHostChunks,
+                             kHostChunks);
 }
 
 // Batched host-buffer sorts: arrays j = 0..count-1 alternate between two
@@ -667,8 +673,13 @@ bitonic_status sort_u32_host_batch_impl(const uint32_t* const* in, uint32_t* con
             const bool tiles = pe && pe->plan.launches[0].kind != KIND_STEP && !pe->opt.pipeline &&
                                pe->plan.descs[pe->plan.launches[0].desc].contiguous;
             if (tiles) {
+                // Once the pipeline is full an array's upload ends long before its
+                // passes start and its download overlaps the next array's
+                // passes: only the first upload and the last download are
+                // chunked (a chunked launch leaves a partial wave per chunk).
+                const int n_up = j == 0 ? kHostChunks : 1, n_down = j + 1 == count ? kHostChunks : 1;
                 if ((st = enqueue_host_sort(*ds, *pe, in[j], out[j], n[j], km, dev, w->up, w->side, w->down, ev_in,
-                                            ev_out)))
+                                            ev_out, n_up, n_down)))
                     return st;
             } else {
                 // upload, sort and download in turn, ordered through the three streams
