@@ -133,22 +133,109 @@ static uint32_t grid_for(uint32_t n)
     return g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g);
 }
 
+// Vector forms of the pair kernels: each thread moves groups of four
+// elements as 16-byte vectors (composites as two 16-byte vectors), so that
+// every SM keeps enough bytes in flight for HBM; the gather issues its four
+// value reads independently.  Used when the key / value pointers are
+// 16-byte aligned (the composite workspace always is); the tail of fewer
+// than four elements is done element by element.
+__global__ void __launch_bounds__(256) k_pairs_pack4(ulonglong2* __restrict__ comp, const uint4* __restrict__ keys,
+                                                     uint32_t n4, uint32_t n, int desc,
+                                                     const uint32_t* __restrict__ keys1, uint64_t* __restrict__ comp1)
+{
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
+        uint4 k = keys[q];
+        if (desc) {
+            k.x = ~k.x; k.y = ~k.y; k.z = ~k.z; k.w = ~k.w;
+        }
+        const uint64_t i = 4ull * q;
+        comp[2 * q] = make_ulonglong2(((uint64_t)k.x << 32) | i, ((uint64_t)k.y << 32) | (i + 1));
+        comp[2 * q + 1] = make_ulonglong2(((uint64_t)k.z << 32) | (i + 2), ((uint64_t)k.w << 32) | (i + 3));
+    }
+    if (blockIdx.x == 0)
+        for (uint32_t i = 4 * n4 + threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t k = desc ? ~keys1[i] : keys1[i];
+            comp1[i] = ((uint64_t)k << 32) | i;
+        }
+}
+
+__global__ void __launch_bounds__(256) k_pairs_gather4(ulonglong2* __restrict__ comp, const uint32_t* __restrict__ vals,
+                                                       uint32_t n4, uint32_t n, uint64_t* __restrict__ comp1)
+{
+    constexpr uint64_t kHi = 0xFFFFFFFF00000000ull;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
+        ulonglong2 a = comp[2 * q], b = comp[2 * q + 1];
+        const uint32_t v0 = vals[(uint32_t)a.x], v1 = vals[(uint32_t)a.y];
+        const uint32_t v2 = vals[(uint32_t)b.x], v3 = vals[(uint32_t)b.y];
+        a.x = (a.x & kHi) | v0; a.y = (a.y & kHi) | v1;
+        b.x = (b.x & kHi) | v2; b.y = (b.y & kHi) | v3;
+        comp[2 * q] = a;
+        comp[2 * q + 1] = b;
+    }
+    if (blockIdx.x == 0)
+        for (uint32_t i = 4 * n4 + threadIdx.x; i < n; i += blockDim.x) {
+            const uint64_t c = comp1[i];
+            comp1[i] = (c & kHi) | vals[(uint32_t)c];
+        }
+}
+
+__global__ void __launch_bounds__(256) k_pairs_unpack4(const ulonglong2* __restrict__ comp, uint4* __restrict__ keys,
+                                                       uint4* __restrict__ vals, uint32_t n4, uint32_t n, int desc,
+                                                       const uint64_t* __restrict__ comp1, uint32_t* __restrict__ keys1,
+                                                       uint32_t* __restrict__ vals1)
+{
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
+        const ulonglong2 a = comp[2 * q], b = comp[2 * q + 1];
+        uint4 k = make_uint4((uint32_t)(a.x >> 32), (uint32_t)(a.y >> 32), (uint32_t)(b.x >> 32), (uint32_t)(b.y >> 32));
+        if (desc) {
+            k.x = ~k.x; k.y = ~k.y; k.z = ~k.z; k.w = ~k.w;
+        }
+        keys[q] = k;
+        vals[q] = make_uint4((uint32_t)a.x, (uint32_t)a.y, (uint32_t)b.x, (uint32_t)b.y);
+    }
+    if (blockIdx.x == 0)
+        for (uint32_t i = 4 * n4 + threadIdx.x; i < n; i += blockDim.x) {
+            const uint64_t c = comp1[i];
+            const uint32_t k = (uint32_t)(c >> 32);
+            keys1[i] = desc ? ~k : k;
+            vals1[i] = (uint32_t)c;
+        }
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
 cudaError_t launch_pairs_pack(uint64_t* comp, const uint32_t* keys, uint32_t n, int desc, cudaStream_t s)
 {
-    k_pairs_pack<<<grid_for(n), 256, 0, s>>>(comp, keys, n, desc);
+    if (aligned16(keys) && aligned16(comp)) {
+        const uint32_t n4 = n / 4;
+        k_pairs_pack4<<<grid_for(n4), 256, 0, s>>>((ulonglong2*)comp, (const uint4*)keys, n4, n, desc, keys, comp);
+    } else {
+        k_pairs_pack<<<grid_for(n), 256, 0, s>>>(comp, keys, n, desc);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_pairs_gather(uint64_t* comp, const uint32_t* vals, uint32_t n, cudaStream_t s)
 {
-    k_pairs_gather<<<grid_for(n), 256, 0, s>>>(comp, vals, n);
+    if (aligned16(comp)) {
+        const uint32_t n4 = n / 4;
+        k_pairs_gather4<<<grid_for(n4), 256, 0, s>>>((ulonglong2*)comp, vals, n4, n, comp);
+    } else {
+        k_pairs_gather<<<grid_for(n), 256, 0, s>>>(comp, vals, n);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_pairs_unpack(const uint64_t* comp, uint32_t* keys, uint32_t* vals, uint32_t n, int desc,
                                 cudaStream_t s)
 {
-    k_pairs_unpack<<<grid_for(n), 256, 0, s>>>(comp, keys, vals, n, desc);
+    if (aligned16(comp) && aligned16(keys) && aligned16(vals)) {
+        const uint32_t n4 = n / 4;
+        k_pairs_unpack4<<<grid_for(n4), 256, 0, s>>>((const ulonglong2*)comp, (uint4*)keys, (uint4*)vals, n4, n,
+                                                     desc, comp, keys, vals);
+    } else {
+        k_pairs_unpack<<<grid_for(n), 256, 0, s>>>(comp, keys, vals, n, desc);
+    }
     return cudaGetLastError();
 }
 
