@@ -213,7 +213,8 @@ typedef enum {
 typedef struct {
     int variant;          /* bitonic_variant */
     int tile_log2;        /* log2 of keys per on-chip tile; 0 = automatic */
-    int global_bits;      /* strides fused per global pass; 0 = automatic */
+    int global_bits;      /* most strides at or above the tile size fused per global pass;
+                             0 = automatic (8) */
     int use_graph;        /* 1 = replay cached CUDA graphs (default), 0 = plain launches */
     int keys_per_thread_log2; /* log2 of keys each thread holds in registers; 0 = automatic */
     int io_direct;        /* bit 0: load a tile straight into its first round's register layout,
