@@ -396,3 +396,53 @@ def test_host_buffer_batch(ascending):
                        [shared, host_tensor(np.zeros(3, np.uint32)), shared], ascending)
     torch.cuda.synchronize()
     assert np.array_equal(shared.numpy().view(np.uint32), oracle.merge_sort(b, ascending))
+
+
+def unsigned_signature(t, chunk=1 << 27):
+    """Multiset signature of a CUDA int32 tensor read as uint32: the 4096-bucket
+    histogram of the top 12 bits, and the sums of the keys and of their
+    squares (modulo 2^64)."""
+    hist = torch.zeros(4096, dtype=torch.int64, device=t.device)
+    s1 = torch.zeros((), dtype=torch.int64, device=t.device)
+    s2 = torch.zeros((), dtype=torch.int64, device=t.device)
+    for c in range(0, t.numel(), chunk):
+        x = t[c:c + chunk].to(torch.int64) & 0xFFFFFFFF
+        hist += torch.bincount(x >> 20, minlength=4096)
+        s1 += x.sum()
+        s2 += (x * x).sum()
+    return hist, int(s1), int(s2)
+
+
+def assert_sorted_unsigned(t, chunk=1 << 27):
+    flip = torch.tensor(-2 ** 31, dtype=torch.int32, device=t.device)
+    prev = None
+    for c in range(0, t.numel(), chunk):
+        u = torch.bitwise_xor(t[c:c + chunk], flip)   # unsigned order as signed order
+        assert bool((u[1:] >= u[:-1]).all()), c
+        if prev is not None:
+            assert int(u[0]) >= prev, c
+        prev = int(u[-1])
+
+
+def test_maximum_size_properties():
+    # The largest supported sort, 2^31 keys (8 GiB), and 2^31 - 5 (a ragged
+    # tail at the limit): too large for the oracle, so checked by properties
+    # that hold at any size -- sorted, the same multiset signature as the
+    # input, and the extremes in place.  Input: a seeded device generator.
+    n = 1 << 31
+    gen = torch.Generator(device="cuda").manual_seed(31)
+    src = torch.randint(-2 ** 31, 2 ** 31, (n,), dtype=torch.int32, device="cuda", generator=gen)
+    for m in (n, n - 5):
+        t = src[:m].clone()
+        bt.sort_(t)
+        torch.cuda.synchronize()
+        assert_sorted_unsigned(t)
+        h_in, a_in, b_in = unsigned_signature(src[:m])
+        h_out, a_out, b_out = unsigned_signature(t)
+        assert torch.equal(h_in, h_out) and a_in == a_out and b_in == b_out, m
+        flipped = torch.bitwise_xor(src[:m], torch.tensor(-2 ** 31, dtype=torch.int32, device="cuda"))
+        lo, hi = int(flipped.min()) + 2 ** 31, int(flipped.max()) + 2 ** 31
+        assert int(t[0]) & 0xFFFFFFFF == lo and int(t[-1]) & 0xFFFFFFFF == hi, m
+        del t, flipped
+    del src
+    torch.cuda.empty_cache()
