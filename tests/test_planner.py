@@ -8,7 +8,7 @@ import pytest
 import oracle
 import paper_1506_01446_gb300 as bt
 import workloads
-from plan_emulator import Stats, emulate
+from plan_emulator import Stats, debug_plan, emulate
 
 pytestmark = pytest.mark.skipif(not __import__("os").path.exists(bt.LIB_PATH),
                                 reason="CUDA library not built")
@@ -49,11 +49,15 @@ def test_other_variants_and_tiles(variant, tile):
             assert np.array_equal(got, oracle.merge_sort(keys)), (variant, tile, n, dist)
 
 
-@pytest.mark.parametrize("tile,kpt", [(14, 6), (14, 5), (13, 5)])
-def test_tile_configurations(tile, kpt):
-    bt.set_options(tile_log2=tile, keys_per_thread_log2=kpt)
+@pytest.mark.parametrize("tile,kpt,cap", [(14, 6, 0), (14, 6, 2), (14, 5, 0), (13, 5, 0)])
+def test_tile_configurations(tile, kpt, cap):
+    bt.set_options(tile_log2=tile, keys_per_thread_log2=kpt, ctas_per_sm=cap)
+    # configuration ids: 7 = 256 x 64 capped for three CTAs, 0 = bounded for
+    # two, 2 = 512 x 32, 1 = 8K keys as 256 x 32
+    expect_cfg = {(14, 6, 0): 7, (14, 6, 2): 0, (14, 5, 0): 2, (13, 5, 0): 1}[(tile, kpt, cap)]
     for n in (3000, 1 << 17):
         keys = workloads.uniform_u32(n, seed=kpt)
+        assert debug_plan(n, 4)["cfg"] == expect_cfg
         got, _, st = emulate(keys, True, 1)
         assert np.array_equal(got, oracle.merge_sort(keys)), (tile, kpt, n)
         assert st.conflicted_quarter_warps == 0
@@ -100,8 +104,9 @@ def test_composite_plan_sorts(n):
     # 64-bit composites (key << 32 | index), the pair sort's working array
     keys = (workloads.uniform_u32(n, seed=n) >> np.uint32(24)).astype(np.uint64)
     comp = (keys << np.uint64(32)) | np.arange(n, dtype=np.uint64)
-    for tile in (0, 12):
-        bt.set_options(tile_log2=tile)
+    # (tile, keys per thread): 8K composites as 256 x 32 (default), 4K as 256 x 16
+    for tile, kpt in ((0, 0), (12, 0)):
+        bt.set_options(tile_log2=tile, keys_per_thread_log2=kpt)
         got, _, st = emulate(comp, True, 0)
         assert np.array_equal(got, np.sort(comp))
         assert st.conflicted_quarter_warps == 0
@@ -130,7 +135,6 @@ def test_split_weighs_transposes():
     # trip inside a pass).  At 2^28 4-byte keys the greedy longest-pass split
     # needs 27 passes and 82 transposes; the weighted split trades one pass
     # for twelve transposes.
-    from plan_emulator import debug_plan
     bt.set_options(variant=0, global_bits=8)
     P = debug_plan(1 << 28, 4)
     transposes = sum(int(P["descs"][L[5]]["nrounds"]) - 1 for L in P["launches"])
