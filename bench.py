@@ -463,15 +463,32 @@ def main():
         # between launches) for the roofline of the dominant kernel
         L = info["launches"]
         per_kind = {}
+        per_launch = [[] for _ in range(L)]
         for i in range(args.steps):
             buf.copy_(pristine)
             evs = [torch.cuda.Event(enable_timing=True) for _ in range(L + 1)]
             kinds = bt.sort_profiled_(buf, evs)
             torch.cuda.synchronize()
             for j in range(L):
-                per_kind.setdefault(kinds[j], []).append(evs[j].elapsed_time(evs[j + 1]))
+                t = evs[j].elapsed_time(evs[j + 1])
+                per_kind.setdefault(kinds[j], []).append(t)
+                per_launch[j].append(t)
         tot = {k: sum(v) for k, v in per_kind.items()}
         dom = max(tot, key=tot.get)
+        # the same launches grouped by their register rounds (steps per round;
+        # rounds are joined by shared-memory transposes), each group's mean
+        # time against the HBM time of one read and write of every key
+        shapes = bt.round_shapes(bt.debug_plan(n, 4))
+        by_shape = {}
+        for j in range(L):
+            by_shape.setdefault((kinds[j], shapes[j]), []).extend(per_launch[j])
+        hbm_ms = 2 * 4 * n / (hbm_gbs * 1e9) * 1e3
+        line_shapes = []
+        for (kd, shp), ts in sorted(by_shape.items(), key=lambda kv: -sum(kv[1])):
+            mean = statistics.mean(ts)
+            line_shapes.append({"kernel": bt.KIND_NAMES[kd], "steps_per_round": list(shp),
+                                "launches": len(ts) // args.steps, "mean_ms": round(mean, 4),
+                                "hbm_time_frac": round(hbm_ms / mean, 3)})
         avg_ms = statistics.mean(per_kind[dom])
         algo_bytes = 2 * 4 * n  # each launch reads and writes every key once
         achieved = algo_bytes / (avg_ms / 1e3) / 1e9
@@ -480,7 +497,8 @@ def main():
                             "frac": achieved / hbm_gbs, "traffic": traffic,
                             "kernel": bt.KIND_NAMES[dom], "launches_per_step": len(per_kind[dom]) // args.steps,
                             "avg_launch_ms": avg_ms, "peak_source": peak_src,
-                            "share": {bt.KIND_NAMES[k]: v / sum(tot.values()) for k, v in tot.items()}}
+                            "share": {bt.KIND_NAMES[k]: v / sum(tot.values()) for k, v in tot.items()},
+                            "by_round_shape": line_shapes}
 
         # end to end through the C ABI on host buffers: one batched call
         # (bitonic_sort_u32_host_batch) sorts the K steps' arrays; every step

@@ -274,7 +274,8 @@ bitonic_status bitonic_sort_u32_profiled(uint32_t *keys, size_t n, int ascending
 
 /*
  * Copies the launch plan of an n-key sort (key_bytes 4: keys, 8: pair
- * composites) under the current options, for inspection and host-side
+ * composites) under the current options (with a size class's tuned options
+ * where bitonic_set_class_options installed some), for inspection and host-side
  * tests.  info (max_info ints) receives N, the tile configuration id, its
  * log2 keys per thread and log2 threads per CTA, the launch count L and the
  * descriptor count D, then 7 ints per launch (kind, phase, hi, lo, flip,

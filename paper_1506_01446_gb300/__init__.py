@@ -287,6 +287,47 @@ def plan_info(n: int, pairs: bool = False) -> dict:
     return dict(zip(("launches", "hbm_passes", "fused_steps", "global_steps"), (x.value for x in out)))
 
 
+def desc_dtype():
+    """numpy layout of one launch descriptor (TileParamsBig in csrc/desc.h)."""
+    import numpy as np
+    rnd = np.dtype([("thr_loc", "<u2", 10), ("reg_loc", "<u2", 5), ("nsteps", "u1"),
+                    ("steps", "u1", 36), ("pattern", "u1")])
+    io = np.dtype([("thr_glob", "<u4", 10), ("reg_glob", "<u4", 5)])
+    return np.dtype([("gvec", "<u4", 16), ("io", io, 2), ("span_mask", "<u4"), ("run_shift", "u1", 4),
+                     ("run_width", "u1", 4), ("m", "u1"), ("nruns", "u1"), ("contiguous", "u1"),
+                     ("nrounds", "u1"), ("row_log", "u1"), ("pad2", "u1", 3), ("rounds", rnd, 100)])
+
+
+def debug_plan(n: int, key_bytes: int = 4) -> dict:
+    """The launch plan the library builds for a sort of n keys of key_bytes
+    bytes under the current options (host code only, no GPU): the tile
+    configuration, per launch (kind, phase, hi, lo, flip, descriptor, grid),
+    and the descriptors."""
+    import numpy as np
+    lib = load()
+    dt = desc_dtype()
+    if lib.bitonic_debug_desc_size() != dt.itemsize:
+        raise RuntimeError("descriptor layout does not match the library")
+    info = (ctypes.c_int * (6 + 7 * 4096))()
+    descs = np.zeros(256, dtype=dt)
+    _check(lib.bitonic_debug_plan(int(n), int(key_bytes), info, len(info), descs.ctypes.data, len(descs)),
+           "bitonic_debug_plan")
+    N, cfg, log_r, log_t, L, D = info[:6]
+    launches = [tuple(info[6 + 7 * i: 13 + 7 * i]) for i in range(L)]
+    return dict(N=N, cfg=cfg, log_r=log_r, log_t=log_t, launches=launches, descs=descs[:D])
+
+
+def round_shapes(plan: dict) -> list:
+    """Per launch of a debug_plan, the number of network steps in each of its
+    register rounds (rounds are joined by a shared-memory transpose; a round
+    without steps only changes the layout for coalesced global access)."""
+    out = []
+    for la in plan["launches"]:
+        d = plan["descs"][la[5]]
+        out.append(tuple(int(d["rounds"][r]["nsteps"]) for r in range(int(d["nrounds"]))))
+    return out
+
+
 def sort_profiled_(keys, events, ascending: bool = True, stream=None):
     """Like sort_ but without a graph, recording events[i] before launch i and
     events[L] after the last; returns the kernel kind of each launch."""

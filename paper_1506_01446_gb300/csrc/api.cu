@@ -789,12 +789,6 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
 
 }  // namespace
 
-Options current_options()
-{
-    std::lock_guard<std::mutex> g(g_mu);
-    return g_opt;
-}
-
 }  // namespace bitonic
 
 using namespace bitonic;
@@ -1054,7 +1048,17 @@ bitonic_status bitonic_debug_plan(size_t n, int key_bytes, int* info, int max_in
                                   int max_descs)
 {
     if (!info || max_info < 6 || (key_bytes != 4 && key_bytes != 8)) return BITONIC_ERR_INVALID;
-    Plan p = make_plan(n < 2 ? 2 : n, key_bytes, current_options());
+    if (n > kMaxKeys) return BITONIC_ERR_UNSUPPORTED;
+    Options o;
+    {
+        // the options the sort itself resolves for this size class
+        std::lock_guard<std::mutex> g(g_mu);
+        uint64_t N = 2;
+        int k = 1;
+        while (N < n) { N <<= 1; ++k; }
+        o = resolve_options(key_bytes, k);
+    }
+    Plan p = make_plan(n < 2 ? 2 : n, key_bytes, o);
     if (!p.ok) return BITONIC_ERR_UNSUPPORTED;
     info[0] = (int)p.N;
     info[1] = p.cfg;

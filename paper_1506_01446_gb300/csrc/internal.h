@@ -61,8 +61,6 @@ struct Options {
     int pipeline = 0;
 };
 
-Options current_options();
-
 // Builds the launch sequence for a sort of n keys of key_bytes bytes.
 Plan make_plan(uint64_t n, int key_bytes, const Options& opt);
 

@@ -10,32 +10,12 @@ the CPU against the oracle before any GPU run.
 """
 from __future__ import annotations
 
-import ctypes
-
 import numpy as np
 
 import paper_1506_01446_gb300 as bt
 
-ROUND_DT = np.dtype([("thr_loc", "<u2", 10), ("reg_loc", "<u2", 5), ("nsteps", "u1"),
-                     ("steps", "u1", 36), ("pattern", "u1")])
-IO_DT = np.dtype([("thr_glob", "<u4", 10), ("reg_glob", "<u4", 5)])
-TILE_DT = np.dtype([("gvec", "<u4", 16), ("io", IO_DT, 2), ("span_mask", "<u4"), ("run_shift", "u1", 4),
-                    ("run_width", "u1", 4),
-                    ("m", "u1"), ("nruns", "u1"), ("contiguous", "u1"), ("nrounds", "u1"),
-                    ("row_log", "u1"), ("pad2", "u1", 3), ("rounds", ROUND_DT, 100)])
-KIND_TILE_SORT, KIND_GLOBAL, KIND_TILE_MERGE, KIND_STEP = range(4)
-
-
-def debug_plan(n: int, key_bytes: int):
-    lib = bt.load()
-    assert lib.bitonic_debug_desc_size() == TILE_DT.itemsize
-    info = (ctypes.c_int * (6 + 7 * 4096))()
-    descs = np.zeros(256, dtype=TILE_DT)
-    st = lib.bitonic_debug_plan(n, key_bytes, info, len(info), descs.ctypes.data, len(descs))
-    assert st == 0, bt.status_string(st)
-    N, cfg, log_r, log_t, L, D = info[:6]
-    launches = [tuple(info[6 + 7 * i: 13 + 7 * i]) for i in range(L)]
-    return dict(N=N, cfg=cfg, log_r=log_r, log_t=log_t, launches=launches, descs=descs[:D])
+KIND_STEP = 3  # one-step kernel (the launch kinds of bitonic_debug_plan)
+debug_plan = bt.debug_plan
 
 
 def _xor_span(vectors, count_bits):

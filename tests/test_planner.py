@@ -141,3 +141,19 @@ def test_split_weighs_transposes():
     assert len(P["launches"]) <= 28
     assert 4 * len(P["launches"]) + transposes <= 4 * 27 + 82 - 8
     assert transposes <= 70
+
+
+def test_debug_plan_follows_class_options():
+    # bitonic_debug_plan reports the plan the sort itself would run: a size
+    # class's tuned options (here 8K-key tiles for 2^20 keys) apply to that
+    # class only
+    bt.set_options(tile_log2=0, keys_per_thread_log2=0, ctas_per_sm=0)
+    try:
+        bt.set_class_options(4, 20, dict(tile_log2=13, keys_per_thread_log2=5, l2_prefetch=1))
+        assert debug_plan(1 << 20, 4)["cfg"] == 1
+        assert debug_plan((1 << 19) + 1, 4)["cfg"] == 1
+        assert debug_plan(1 << 21, 4)["cfg"] == 7
+        assert debug_plan(1 << 20, 8)["cfg"] == 4
+    finally:
+        bt.set_class_options(4, 20, None)
+    assert debug_plan(1 << 20, 4)["cfg"] == 7
