@@ -223,8 +223,7 @@ typedef struct {
     int ctas_per_sm;      /* tile kernels: 3 = registers capped for three resident CTAs per SM
                              where such a kernel exists for the tile shape, else two;
                              2 = registers bounded for two CTAs where such a kernel exists,
-                             else not bounded; 0 = automatic (3 for 4-byte
-                             keys, 2 for 8-byte keys and composites; default) */
+                             else not bounded; 0 = automatic (2; default) */
     int min_row_log2;     /* shortest run of consecutive keys a multi-stride pass moves, log2
                              (keys); 0 = 128 bytes.  Shorter rows fit one more stride per pass. */
     int l2_prefetch;      /* > 0: each tile CTA asks the TMA unit to prefetch into L2 the tile

@@ -291,7 +291,7 @@ def desc_dtype():
     """numpy layout of one launch descriptor (TileParamsBig in csrc/desc.h)."""
     import numpy as np
     rnd = np.dtype([("thr_loc", "<u2", 10), ("reg_loc", "<u2", 5), ("nsteps", "u1"),
-                    ("steps", "u1", 36), ("pattern", "u1")])
+                    ("steps", "u1", 36), ("pattern", "u1"), ("thr_sw", "<u2", 10), ("reg_sw", "<u2", 5)])
     io = np.dtype([("thr_glob", "<u4", 10), ("reg_glob", "<u4", 5)])
     return np.dtype([("gvec", "<u4", 16), ("io", io, 2), ("span_mask", "<u4"), ("run_shift", "u1", 4),
                      ("run_width", "u1", 4), ("m", "u1"), ("nruns", "u1"), ("contiguous", "u1"),

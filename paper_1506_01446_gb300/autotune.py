@@ -25,6 +25,7 @@ CANDIDATES_U32 = (
     dict(tile_log2=14, keys_per_thread_log2=6, global_bits=8, l2_prefetch=1, ctas_per_sm=3),
     dict(tile_log2=14, keys_per_thread_log2=6, global_bits=0, l2_prefetch=1, ctas_per_sm=3),
     dict(tile_log2=14, keys_per_thread_log2=6, global_bits=8, l2_prefetch=1, ctas_per_sm=2),
+    dict(tile_log2=14, keys_per_thread_log2=6, global_bits=0, l2_prefetch=1, ctas_per_sm=2),
     dict(tile_log2=14, keys_per_thread_log2=6, global_bits=8, l2_prefetch=0, ctas_per_sm=3),
     dict(tile_log2=13, keys_per_thread_log2=5, global_bits=0, l2_prefetch=1, ctas_per_sm=2),
 )

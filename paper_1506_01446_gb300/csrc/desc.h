@@ -37,12 +37,34 @@ constexpr int kMaxCtaRuns = 4;
 // Step code: register-index bit q in bits 0..3, kStepFlip set for a mirror step.
 constexpr uint8_t kStepFlip = 16;
 
+#if defined(__CUDACC__)
+#define BITONIC_HD __host__ __device__
+#else
+#define BITONIC_HD
+#endif
+
+// Shared-memory swizzle on vector indices: the low 3 bits (the 16-byte bank
+// group within a 128-byte line) are XORed with every higher 3-bit group.
+// Linear over GF(2), so phys(a ^ b) = phys(a) ^ phys(b).  A quarter warp
+// whose 3 lane bits sit on local vector bits of distinct residue mod 3 hits 8
+// distinct bank groups.
+BITONIC_HD constexpr uint32_t smem_swizzle(uint32_t lv)
+{
+    return lv ^ (((lv >> 3) ^ (lv >> 6) ^ (lv >> 9) ^ (lv >> 12) ^ (lv >> 15)) & 7u);
+}
+
 struct RoundDesc {
     uint16_t thr_loc[kMaxLogThreads];  // local vector of thread-index bit i
     uint16_t reg_loc[kMaxRegBits];     // local vector of register bit VB + j
     uint8_t nsteps;
     uint8_t steps[kMaxStepsPerRound];
     uint8_t pattern;                   // index into the round-pattern catalog, 0xFF = generic
+    // Shared-memory vector slots, precomputed by the planner:
+    // smem_swizzle(thr_loc[i] >> VB) and smem_swizzle(reg_loc[j] >> VB).  By
+    // linearity a thread's vector v sits at the XOR of thr_sw over the set bits
+    // of the thread index and of reg_sw over the set bits of v.
+    uint16_t thr_sw[kMaxLogThreads];
+    uint16_t reg_sw[kMaxRegBits];
 };
 
 // Global-memory side of the first (load) and last (store) rounds.

@@ -31,16 +31,6 @@ struct KeyTraits<uint64_t> {
     static constexpr uint64_t kMax = 0xFFFFFFFFFFFFFFFFull;
 };
 
-// Shared-memory swizzle on vector indices: the low 3 bits (the 16-byte bank
-// group within a 128-byte line) are XORed with every higher 3-bit group.
-// Linear over GF(2), so phys(a ^ b) = phys(a) ^ phys(b).  A quarter warp
-// whose 3 lane bits sit on local vector bits of distinct residue mod 3 hits 8
-// distinct bank groups.
-__device__ __forceinline__ uint32_t swz(uint32_t lv)
-{
-    uint32_t f = (lv >> 3) ^ (lv >> 6) ^ (lv >> 9) ^ (lv >> 12) ^ (lv >> 15);
-    return lv ^ (f & 7u);
-}
 
 // Multipliers 1 and 2^32 - 1 for the multiply-add form of a 4-byte
 // compare-exchange.  Read from constant memory, so the compiler cannot turn
@@ -133,6 +123,18 @@ __device__ __forceinline__ uint32_t thread_local_index(const RoundDesc& rd, uint
     for (int i = 0; i < LOG_T; ++i)
         if ((x >> i) & 1u) L ^= rd.thr_loc[i];
     return L;
+}
+
+// Thread part of a round's swizzled shared-memory vector slot: XOR of
+// thr_sw[i] over set bits i of x.
+template <int LOG_T>
+__device__ __forceinline__ uint32_t thread_smem_slot(const RoundDesc& rd, uint32_t x)
+{
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < LOG_T; ++i)
+        if ((x >> i) & 1u) s ^= rd.thr_sw[i];
+    return s;
 }
 
 // Register part of vector v's local index (v indexes the R / VEC vectors).
@@ -301,12 +303,10 @@ struct Tile {
     // Shared-memory addresses (in vectors) of this thread's vectors under rd.
     __device__ __forceinline__ void smem_write(Vec* sm, const RoundDesc& rd, uint32_t x)
     {
-        uint32_t rv[NREG];
-        load_reg_vectors(rd, rv);
         uint32_t pr[NREG];
 #pragma unroll
-        for (int j = 0; j < NREG; ++j) pr[j] = swz(rv[j] >> VB);
-        const uint32_t pt = swz(thread_local_index<LOG_T>(rd, x) >> VB);
+        for (int j = 0; j < NREG; ++j) pr[j] = rd.reg_sw[j];
+        const uint32_t pt = thread_smem_slot<LOG_T>(rd, x);
 #pragma unroll
         for (int v = 0; v < NV; ++v) sm[pt ^ reg_local_index<NREG>(pr, v)] = regs_to_vec<K>(r + v * VEC);
     }
@@ -371,12 +371,10 @@ struct Tile {
 
     __device__ __forceinline__ void smem_read(const Vec* sm, const RoundDesc& rd, uint32_t x)
     {
-        uint32_t rv[NREG];
-        load_reg_vectors(rd, rv);
         uint32_t pr[NREG];
 #pragma unroll
-        for (int j = 0; j < NREG; ++j) pr[j] = swz(rv[j] >> VB);
-        const uint32_t pt = swz(thread_local_index<LOG_T>(rd, x) >> VB);
+        for (int j = 0; j < NREG; ++j) pr[j] = rd.reg_sw[j];
+        const uint32_t pt = thread_smem_slot<LOG_T>(rd, x);
 #pragma unroll
         for (int v = 0; v < NV; ++v) vec_to_regs<K>(sm[pt ^ reg_local_index<NREG>(pr, v)], r + v * VEC);
     }

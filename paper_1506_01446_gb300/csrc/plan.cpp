@@ -148,6 +148,8 @@ bool emit_round(const HostRound& hr, int log_t, int m, int vb, RoundDesc& rd)
         if (hr.R[q] == hr.mirror_bit) v |= hr.mirror;
         rd.reg_loc[q] = (uint16_t)v;
     }
+    for (int t = 0; t < log_t; ++t) rd.thr_sw[t] = (uint16_t)smem_swizzle(rd.thr_loc[t] >> vb);
+    for (size_t q = 0; q < hr.R.size(); ++q) rd.reg_sw[q] = (uint16_t)smem_swizzle(rd.reg_loc[q] >> vb);
     if (hr.steps.size() > (size_t)kMaxStepsPerRound) return false;
     rd.nsteps = (uint8_t)hr.steps.size();
     for (size_t s = 0; s < hr.steps.size(); ++s) {
@@ -299,12 +301,13 @@ int choose_cfg(int key_bytes, const Options& opt)
     // the largest configured value below that.
     const int pref_r = opt.keys_per_thread_log2 ? opt.keys_per_thread_log2 : (key_bytes == 4 ? 6 : 5);
     // Register cap: 3 = kernels capped for three resident CTAs per SM, 2 =
-    // kernels bounded for two; 0 = automatic: three for 4-byte keys (4%
-    // faster at 2^24, within 1% at 2^28 on GB300), two for 8-byte keys (2^26
-    // uint64: 7.84 ms against 8.35 ms for the capped kernel, which spills).
-    // A cap is taken where a capped kernel of this shape exists; other shapes
-    // fall back to the two-CTA kernel.
-    const int cap = opt.ctas_per_sm ? opt.ctas_per_sm : (key_bytes == 4 ? 3 : 2);
+    // kernels bounded for two; 0 = automatic: two.  Measured on GB300 with the
+    // shared-memory slots precomputed by the planner: 2^28 4-byte keys 12.54
+    // against 12.73 ms, 2^22 0.169 against 0.180 ms (three CTAs win only
+    // where the keys fit in L2: 2^24 0.647 against 0.631 ms); 2^26 pairs 8.79
+    // against 9.47 ms.  A cap is taken where a capped kernel of this shape
+    // exists; other shapes fall back to the two-CTA kernel.
+    const int cap = opt.ctas_per_sm ? opt.ctas_per_sm : 2;
     const int want_blocks = cap == 3 ? 3 : 1;
     for (int blocks : {want_blocks, 1}) {
         int best = -1;

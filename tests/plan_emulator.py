@@ -132,9 +132,14 @@ def emulate(keys: np.ndarray, ascending: bool = True, front: int = 0, stats: Sta
         rounds = P["rounds"][:nr]
         c = int(P["row_log"])
         layouts = [_round_local(rd, log_r, log_t, vb) for rd in rounds]
-        for Lr in layouts:
+        for rd, Lr in zip(rounds, layouts):
             assert np.array_equal(np.sort(Lr.ravel()), np.arange(1 << m)), "round layout not a bijection"
             _check_banks(Lr, vb, stats)
+            # the planner's precomputed shared-memory slots: thread part XOR
+            # register part must equal the swizzle of every vector's local index
+            slot = (_xor_span(rd["thr_sw"], log_t)[:, None]
+                    ^ _xor_span(rd["reg_sw"], log_r - vb)[None, :])
+            assert np.array_equal(slot, _swz(Lr[:, ::(1 << vb)] >> vb)), "shared-memory slots"
         for idx in (0, nr - 1):
             thr = rounds[idx]["thr_loc"]
             need = min(3, c - vb)

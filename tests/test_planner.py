@@ -49,12 +49,12 @@ def test_other_variants_and_tiles(variant, tile):
             assert np.array_equal(got, oracle.merge_sort(keys)), (variant, tile, n, dist)
 
 
-@pytest.mark.parametrize("tile,kpt,cap", [(14, 6, 0), (14, 6, 2), (14, 5, 0), (13, 5, 0)])
+@pytest.mark.parametrize("tile,kpt,cap", [(14, 6, 0), (14, 6, 3), (14, 5, 0), (13, 5, 0)])
 def test_tile_configurations(tile, kpt, cap):
     bt.set_options(tile_log2=tile, keys_per_thread_log2=kpt, ctas_per_sm=cap)
-    # configuration ids: 7 = 256 x 64 capped for three CTAs, 0 = bounded for
-    # two, 2 = 512 x 32, 1 = 8K keys as 256 x 32
-    expect_cfg = {(14, 6, 0): 7, (14, 6, 2): 0, (14, 5, 0): 2, (13, 5, 0): 1}[(tile, kpt, cap)]
+    # configuration ids: 0 = 256 x 64 bounded for two CTAs (the default), 7 =
+    # capped for three, 2 = 512 x 32, 1 = 8K keys as 256 x 32
+    expect_cfg = {(14, 6, 0): 0, (14, 6, 3): 7, (14, 5, 0): 2, (13, 5, 0): 1}[(tile, kpt, cap)]
     for n in (3000, 1 << 17):
         keys = workloads.uniform_u32(n, seed=kpt)
         assert debug_plan(n, 4)["cfg"] == expect_cfg
@@ -152,8 +152,8 @@ def test_debug_plan_follows_class_options():
         bt.set_class_options(4, 20, dict(tile_log2=13, keys_per_thread_log2=5, l2_prefetch=1))
         assert debug_plan(1 << 20, 4)["cfg"] == 1
         assert debug_plan((1 << 19) + 1, 4)["cfg"] == 1
-        assert debug_plan(1 << 21, 4)["cfg"] == 7
+        assert debug_plan(1 << 21, 4)["cfg"] == 0
         assert debug_plan(1 << 20, 8)["cfg"] == 4
     finally:
         bt.set_class_options(4, 20, None)
-    assert debug_plan(1 << 20, 4)["cfg"] == 7
+    assert debug_plan(1 << 20, 4)["cfg"] == 0
