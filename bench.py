@@ -442,8 +442,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (splitmix64 uniform uint32, input restored before every step, untimed)",
         "config": {"workload": f"single uint32 array, n=2^{args.n_log2}, uniform random, ascending",
-                   "n": n, "l2": "inputs larger than L2 (1 GiB per array)" if n >= 1 << 26 else
-                   "input restored by a copy before each step", "parallelism": f"replicas x{world}",
+                   "n": n, "l2": (f"inputs larger than L2 ({4 * n / 2**20:.0f} MiB per array)" if 4 * n > 129 << 20
+                                  else "input restored by a copy before each step"),
+                   "parallelism": f"replicas x{world}",
                    "plan": info, "tuned": tuned},
         "gpu_launches": info["launches"] * args.steps,
         "clocks": clk.summary(),
