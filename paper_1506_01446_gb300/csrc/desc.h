@@ -59,10 +59,11 @@ struct RoundDesc {
     uint8_t nsteps;
     uint8_t steps[kMaxStepsPerRound];
     uint8_t pattern;                   // index into the round-pattern catalog, 0xFF = generic
-    // Shared-memory vector slots, precomputed by the planner:
-    // smem_swizzle(thr_loc[i] >> VB) and smem_swizzle(reg_loc[j] >> VB).  By
-    // linearity a thread's vector v sits at the XOR of thr_sw over the set bits
-    // of the thread index and of reg_sw over the set bits of v.
+    // Byte offsets of the 16-byte shared-memory vector slots, precomputed by
+    // the planner: smem_swizzle(thr_loc[i] >> VB) * 16 and
+    // smem_swizzle(reg_loc[j] >> VB) * 16.  By linearity a thread's vector v
+    // sits at the XOR of thr_sw over the set bits of the thread index and of
+    // reg_sw over the set bits of v (tiles of at most 64 KiB: 16-bit offsets).
     uint16_t thr_sw[kMaxLogThreads];
     uint16_t reg_sw[kMaxRegBits];
 };

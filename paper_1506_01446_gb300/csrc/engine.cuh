@@ -125,7 +125,7 @@ __device__ __forceinline__ uint32_t thread_local_index(const RoundDesc& rd, uint
     return L;
 }
 
-// Thread part of a round's swizzled shared-memory vector slot: XOR of
+// Thread part of a round's shared-memory slot (a byte offset): XOR of
 // thr_sw[i] over set bits i of x.
 template <int LOG_T>
 __device__ __forceinline__ uint32_t thread_smem_slot(const RoundDesc& rd, uint32_t x)
@@ -307,8 +307,10 @@ struct Tile {
 #pragma unroll
         for (int j = 0; j < NREG; ++j) pr[j] = rd.reg_sw[j];
         const uint32_t pt = thread_smem_slot<LOG_T>(rd, x);
+        unsigned char* sb = reinterpret_cast<unsigned char*>(sm);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sm[pt ^ reg_local_index<NREG>(pr, v)] = regs_to_vec<K>(r + v * VEC);
+        for (int v = 0; v < NV; ++v)
+            *reinterpret_cast<Vec*>(sb + (pt ^ reg_local_index<NREG>(pr, v))) = regs_to_vec<K>(r + v * VEC);
     }
 
     // Global load / store for tiles that lie wholly inside [lo, hi).
@@ -375,8 +377,10 @@ struct Tile {
 #pragma unroll
         for (int j = 0; j < NREG; ++j) pr[j] = rd.reg_sw[j];
         const uint32_t pt = thread_smem_slot<LOG_T>(rd, x);
+        const unsigned char* sb = reinterpret_cast<const unsigned char*>(sm);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) vec_to_regs<K>(sm[pt ^ reg_local_index<NREG>(pr, v)], r + v * VEC);
+        for (int v = 0; v < NV; ++v)
+            vec_to_regs<K>(*reinterpret_cast<const Vec*>(sb + (pt ^ reg_local_index<NREG>(pr, v))), r + v * VEC);
     }
 };
 

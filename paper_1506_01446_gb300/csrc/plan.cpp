@@ -148,8 +148,10 @@ bool emit_round(const HostRound& hr, int log_t, int m, int vb, RoundDesc& rd)
         if (hr.R[q] == hr.mirror_bit) v |= hr.mirror;
         rd.reg_loc[q] = (uint16_t)v;
     }
-    for (int t = 0; t < log_t; ++t) rd.thr_sw[t] = (uint16_t)smem_swizzle(rd.thr_loc[t] >> vb);
-    for (size_t q = 0; q < hr.R.size(); ++q) rd.reg_sw[q] = (uint16_t)smem_swizzle(rd.reg_loc[q] >> vb);
+    // 16-byte vector slots as byte offsets (m - vb <= 12 slot bits: below 64 KiB)
+    if (m - vb > 12) return false;
+    for (int t = 0; t < log_t; ++t) rd.thr_sw[t] = (uint16_t)(smem_swizzle(rd.thr_loc[t] >> vb) << 4);
+    for (size_t q = 0; q < hr.R.size(); ++q) rd.reg_sw[q] = (uint16_t)(smem_swizzle(rd.reg_loc[q] >> vb) << 4);
     if (hr.steps.size() > (size_t)kMaxStepsPerRound) return false;
     rd.nsteps = (uint8_t)hr.steps.size();
     for (size_t s = 0; s < hr.steps.size(); ++s) {

@@ -135,11 +135,12 @@ def emulate(keys: np.ndarray, ascending: bool = True, front: int = 0, stats: Sta
         for rd, Lr in zip(rounds, layouts):
             assert np.array_equal(np.sort(Lr.ravel()), np.arange(1 << m)), "round layout not a bijection"
             _check_banks(Lr, vb, stats)
-            # the planner's precomputed shared-memory slots: thread part XOR
-            # register part must equal the swizzle of every vector's local index
+            # the planner's precomputed shared-memory slots (byte offsets of
+            # 16-byte vectors): thread part XOR register part must equal the
+            # swizzle of every vector's local index, times 16
             slot = (_xor_span(rd["thr_sw"], log_t)[:, None]
                     ^ _xor_span(rd["reg_sw"], log_r - vb)[None, :])
-            assert np.array_equal(slot, _swz(Lr[:, ::(1 << vb)] >> vb)), "shared-memory slots"
+            assert np.array_equal(slot, _swz(Lr[:, ::(1 << vb)] >> vb) << 4), "shared-memory slots"
         for idx in (0, nr - 1):
             thr = rounds[idx]["thr_loc"]
             need = min(3, c - vb)
