@@ -3,10 +3,10 @@ the fastest.
 
 A candidate is a tile size (tile_log2), keys held per thread in registers
 (keys_per_thread_log2), the fused-stride cutoff (global_bits: the most
-strides at or above the tile size one pass may take; 0 = as many as fit) and
-the L2 prefetch distance (l2_prefetch, in resident waves) and the register
-cap (ctas_per_sm: 3 = kernels capped for three resident CTAs per SM, 2 =
-uncapped).
+strides at or above the tile size one pass may take; 0 = automatic, 8), the
+L2 prefetch distance (l2_prefetch, in resident waves) and the register cap
+(ctas_per_sm: 3 = kernels capped for three resident CTAs per SM, 2 = kernels
+bounded for two, the default).
 For every size class 2^k the tuner times each candidate with CUDA events on
 data already in device memory, picks the fastest, installs it with
 bitonic_set_class_options and caches the choices as JSON per GPU name (path:
