@@ -157,3 +157,18 @@ def test_debug_plan_follows_class_options():
     finally:
         bt.set_class_options(4, 20, None)
     assert debug_plan(1 << 20, 4)["cfg"] == 0
+
+
+def test_round_shapes_cover_every_step():
+    # The descriptors' register rounds hold every step of the network once:
+    # k(k+1)/2 steps for 2^k keys (Section 3.2), 105 of them (phases 1..14)
+    # in the tile sort, and every launch of the optimized plan at 2^28 is a
+    # tile pass of at most 14 steps after it.
+    bt.set_options(variant=0, tile_log2=0, keys_per_thread_log2=0, ctas_per_sm=0, global_bits=0)
+    for k, kb in ((16, 4), (20, 4), (28, 4), (20, 8), (26, 8)):
+        shapes = bt.round_shapes(bt.debug_plan(1 << k, kb))
+        assert sum(sum(s) for s in shapes) == k * (k + 1) // 2, (k, kb)
+    shapes = bt.round_shapes(bt.debug_plan(1 << 28, 4))
+    assert sum(shapes[0]) == 14 * 15 // 2
+    assert all(sum(s) <= 14 for s in shapes[1:])
+    assert len(shapes) == bt.plan_info(1 << 28)["launches"]
