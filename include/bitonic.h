@@ -171,6 +171,24 @@ bitonic_status bitonic_sort_segmented_pairs_u32(uint32_t *keys, uint32_t *vals,
                                                 bitonic_stream_t stream);
 
 /*
+ * Segmented sorts in either direction: ascending != 0 is the same call as
+ * bitonic_sort_segmented_u32 / bitonic_sort_segmented_pairs_u32; ascending == 0
+ * sorts every segment descending (pairs: by key descending, equal keys in
+ * ascending original index, as bitonic_sort_pairs_u32 orders them).  A
+ * descending sort complements the keys of [offsets[0], offsets[nseg]) on the
+ * caller's stream, sorts ascending and complements them back: keys outside
+ * that span are not touched (Section 3.1: the network sorts either way).
+ * Argument errors, and a pair sort on a capturing stream, are reported
+ * before any key changes.  After a later failure the second complement still
+ * runs, so a sort that launched nothing leaves the keys as they were.
+ */
+bitonic_status bitonic_sort_segmented_u32_dir(uint32_t *keys, const int32_t *offsets, int nseg,
+                                              int ascending, bitonic_stream_t stream);
+bitonic_status bitonic_sort_segmented_pairs_u32_dir(uint32_t *keys, uint32_t *vals,
+                                                    const int32_t *offsets, int nseg, int ascending,
+                                                    bitonic_stream_t stream);
+
+/*
  * bitonic_sort_segmented_pairs_u32 for callers that know every segment is at
  * most max_len pairs long.  With max_len <= 8192 (one packed tile of 64-bit
  * composites) no segment needs the composite workspace, so nothing is read

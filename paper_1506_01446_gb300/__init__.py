@@ -31,6 +31,7 @@ EXPORTS = (
     "bitonic_debug_desc_size", "bitonic_sort_pairs_u32_noalloc", "bitonic_sort_segmented_pairs_u32_bounded",
     "bitonic_set_class_options", "bitonic_sort_i32", "bitonic_sort_f32", "bitonic_sort_u64", "bitonic_sort_i64",
     "bitonic_sort_f64", "bitonic_sort_u32_host", "bitonic_sort_u32_host_batch",
+    "bitonic_sort_segmented_u32_dir", "bitonic_sort_segmented_pairs_u32_dir",
 )
 
 # torch dtype name -> C entry point of the keys-only sorts (uint64 keys may be
@@ -76,6 +77,8 @@ def load() -> ctypes.CDLL:
     lib.bitonic_sort_pairs_u32.argtypes = [vp, vp, sz, i32, vp]
     lib.bitonic_sort_segmented_u32.argtypes = [vp, vp, i32, vp]
     lib.bitonic_sort_segmented_pairs_u32.argtypes = [vp, vp, vp, i32, vp]
+    lib.bitonic_sort_segmented_u32_dir.argtypes = [vp, vp, i32, i32, vp]
+    lib.bitonic_sort_segmented_pairs_u32_dir.argtypes = [vp, vp, vp, i32, i32, vp]
     lib.bitonic_status_string.argtypes = [i32]
     lib.bitonic_status_string.restype = ctypes.c_char_p
     lib.bitonic_last_error_message.argtypes = []
@@ -215,19 +218,29 @@ def _offsets_ptr(offsets):
     return offsets.data_ptr()
 
 
-def sort_segmented_(keys, offsets, stream=None):
-    """Sorts keys[offsets[s]:offsets[s+1]] ascending for every segment s."""
+def sort_segmented_(keys, offsets, stream=None, ascending: bool = True):
+    """Sorts keys[offsets[s]:offsets[s+1]] for every segment s (ascending, or
+    descending through bitonic_sort_segmented_u32_dir)."""
     nseg = offsets.numel() - 1
-    _check(load().bitonic_sort_segmented_u32(_u32_ptr(keys, "keys"), _offsets_ptr(offsets), nseg,
-                                             _stream_handle(stream)), "bitonic_sort_segmented_u32")
+    if ascending:
+        _check(load().bitonic_sort_segmented_u32(_u32_ptr(keys, "keys"), _offsets_ptr(offsets), nseg,
+                                                 _stream_handle(stream)), "bitonic_sort_segmented_u32")
+    else:
+        _check(load().bitonic_sort_segmented_u32_dir(_u32_ptr(keys, "keys"), _offsets_ptr(offsets), nseg, 0,
+                                                     _stream_handle(stream)), "bitonic_sort_segmented_u32_dir")
     return keys
 
 
-def sort_segmented_pairs_(keys, vals, offsets, stream=None):
+def sort_segmented_pairs_(keys, vals, offsets, stream=None, ascending: bool = True):
     nseg = offsets.numel() - 1
-    _check(load().bitonic_sort_segmented_pairs_u32(_u32_ptr(keys, "keys"), _u32_ptr(vals, "vals"),
-                                                   _offsets_ptr(offsets), nseg, _stream_handle(stream)),
-           "bitonic_sort_segmented_pairs_u32")
+    if ascending:
+        _check(load().bitonic_sort_segmented_pairs_u32(_u32_ptr(keys, "keys"), _u32_ptr(vals, "vals"),
+                                                       _offsets_ptr(offsets), nseg, _stream_handle(stream)),
+               "bitonic_sort_segmented_pairs_u32")
+    else:
+        _check(load().bitonic_sort_segmented_pairs_u32_dir(_u32_ptr(keys, "keys"), _u32_ptr(vals, "vals"),
+                                                           _offsets_ptr(offsets), nseg, 0, _stream_handle(stream)),
+               "bitonic_sort_segmented_pairs_u32_dir")
     return keys, vals
 
 

@@ -787,6 +787,43 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
     return BITONIC_OK;
 }
 
+// Segmented sort in either direction.  Descending: complement the keys of
+// the segments' span, sort ascending, complement back (three launches on the
+// caller's stream).  Every argument is checked before a key changes.
+bitonic_status sort_segmented_dir_impl(uint32_t* keys, uint32_t* vals, const int32_t* offsets, int nseg,
+                                       int ascending, cudaStream_t s)
+{
+    if (ascending) return sort_segmented_impl(keys, vals, offsets, nseg, s);
+    if (nseg < 0 || !offsets) {
+        t_last_error = "negative segment count or null offsets";
+        return BITONIC_ERR_INVALID;
+    }
+    if (nseg == 0) return BITONIC_OK;
+    bitonic_status st = check_keys_ptr(keys);
+    if (st) return st;
+    if (vals && (st = check_keys_ptr(vals))) return st;
+    if ((uintptr_t)offsets & 3u) return BITONIC_ERR_INVALID;
+    if (vals && stream_capturing(s)) {
+        t_last_error = "segmented pair sort reads its segment sizes back and cannot be captured";
+        return BITONIC_ERR_UNSUPPORTED;
+    }
+    int grid;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        DeviceState* ds;
+        if ((st = device_state(&ds))) return st;
+        grid = 4 * ds->num_sms;
+    }
+    BT_CK(seg_launch_complement(keys, offsets, nseg, grid, s));
+    st = sort_segmented_impl(keys, vals, offsets, nseg, s);
+    // complement back also after a failed sort, so that a sort that launched
+    // nothing leaves the keys as they were
+    const cudaError_t e = seg_launch_complement(keys, offsets, nseg, grid, s);
+    if (st) return st;
+    BT_CK(e);
+    return BITONIC_OK;
+}
+
 }  // namespace
 
 }  // namespace bitonic
@@ -854,6 +891,19 @@ bitonic_status bitonic_sort_segmented_pairs_u32(uint32_t* keys, uint32_t* vals, 
 {
     if (!vals && nseg > 0) return BITONIC_ERR_INVALID;
     return sort_segmented_impl(keys, vals, offsets, nseg, (cudaStream_t)stream);
+}
+
+bitonic_status bitonic_sort_segmented_u32_dir(uint32_t* keys, const int32_t* offsets, int nseg, int ascending,
+                                              bitonic_stream_t stream)
+{
+    return sort_segmented_dir_impl(keys, nullptr, offsets, nseg, ascending, (cudaStream_t)stream);
+}
+
+bitonic_status bitonic_sort_segmented_pairs_u32_dir(uint32_t* keys, uint32_t* vals, const int32_t* offsets,
+                                                    int nseg, int ascending, bitonic_stream_t stream)
+{
+    if (!vals && nseg > 0) return BITONIC_ERR_INVALID;
+    return sort_segmented_dir_impl(keys, vals, offsets, nseg, ascending, (cudaStream_t)stream);
 }
 
 bitonic_status bitonic_sort_segmented_pairs_u32_bounded(uint32_t* keys, uint32_t* vals, const int32_t* offsets,

@@ -42,5 +42,7 @@ cudaError_t seg_launch_large(uint32_t* keys, uint32_t* vals, const int32_t* offs
                              int32_t comp_base, int grid, cudaStream_t s);
 // out[0] = offsets[0], out[1] = offsets[nseg], out[2] = longest segment.
 cudaError_t seg_launch_stats(const int32_t* offs, int nseg, int* out, cudaStream_t s);
+// keys[i] = ~keys[i] for i in [offsets[0], offsets[nseg]) (grid-stride).
+cudaError_t seg_launch_complement(uint32_t* keys, const int32_t* offs, int nseg, int grid, cudaStream_t s);
 
 }  // namespace bitonic

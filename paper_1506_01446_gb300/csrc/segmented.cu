@@ -102,9 +102,27 @@ __global__ void k_seg_stats(const int32_t* __restrict__ offs, int nseg, int* out
     }
 }
 
+// Complements every key of the segments' span [offs[0], offs[nseg]): a
+// descending segmented sort is the ascending sort of the complemented keys
+// (Section 3.1 sorts either way; ties of pairs stay ordered by index).
+__global__ void k_seg_complement(uint32_t* __restrict__ keys, const int32_t* __restrict__ offs, int nseg)
+{
+    int64_t lo = offs[0];
+    const int64_t hi = offs[nseg];
+    if (lo < 0) lo = 0;  // offsets are non-negative by contract
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += stride) keys[i] = ~keys[i];
+}
+
 }  // namespace
 
 cudaError_t seg_init_attributes() { return seg_tiles_init_attributes(); }
+
+cudaError_t seg_launch_complement(uint32_t* keys, const int32_t* offs, int nseg, int grid, cudaStream_t s)
+{
+    k_seg_complement<<<grid, 256, 0, s>>>(keys, offs, nseg);
+    return cudaGetLastError();
+}
 
 cudaError_t seg_launch_large(uint32_t* keys, uint32_t* vals, const int32_t* offs, void* ws, uint64_t* comp,
                              int32_t comp_base, int grid, cudaStream_t s)

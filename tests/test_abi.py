@@ -45,6 +45,15 @@ def test_argument_errors_need_no_gpu():
     assert lib.bitonic_sort_segmented_u32(16, 16, -1, None) == bt.ERR_INVALID
     assert lib.bitonic_sort_segmented_u32(16, 16, 0, None) == bt.OK
     assert lib.bitonic_sort_segmented_pairs_u32(16, None, 16, 3, None) == bt.ERR_INVALID
+    for asc in (1, 0):  # either direction checks every argument before any launch
+        assert lib.bitonic_sort_segmented_u32_dir(16, None, 4, asc, None) == bt.ERR_INVALID
+        assert lib.bitonic_sort_segmented_u32_dir(16, 16, -1, asc, None) == bt.ERR_INVALID
+        assert lib.bitonic_sort_segmented_u32_dir(16, 16, 0, asc, None) == bt.OK
+        assert lib.bitonic_sort_segmented_u32_dir(3, 16, 4, asc, None) == bt.ERR_INVALID    # misaligned keys
+        assert lib.bitonic_sort_segmented_u32_dir(16, 18, 4, asc, None) == bt.ERR_INVALID   # misaligned offsets
+        assert lib.bitonic_sort_segmented_pairs_u32_dir(16, None, 16, 3, asc, None) == bt.ERR_INVALID
+        assert lib.bitonic_sort_segmented_pairs_u32_dir(16, 18, 16, 3, asc, None) == bt.ERR_INVALID
+        assert lib.bitonic_sort_segmented_pairs_u32_dir(16, 16, 16, 0, asc, None) == bt.OK
     assert lib.bitonic_sort_u32_profiled(16, 100, 1, None, None, 0, None) == bt.ERR_INVALID
     assert lib.bitonic_sort_u32_host(None, None, 0, 1, None) == bt.OK
     assert lib.bitonic_sort_u32_host(None, 16, 10, 1, None) == bt.ERR_INVALID

@@ -214,6 +214,45 @@ def test_segmented_edge_cases(pairs):
     check_segmented(keys, offs, pairs)
 
 
+def check_segmented_descending(keys, offs, pairs):
+    # expected: every segment sorted descending by the oracle (pairs: equal
+    # keys in ascending original index); keys outside the span untouched
+    tk = to_dev(keys)
+    to = torch.from_numpy(offs).cuda()
+    wk = keys.copy()
+    if pairs:
+        vals = workloads.uniform_u32(keys.size, seed=78)
+        tv = to_dev(vals)
+        bt.sort_segmented_pairs_(tk, tv, to, ascending=False)
+        wv = vals.copy()
+        for a, b in zip(offs[:-1], offs[1:]):
+            if b > a:
+                wk[a:b], wv[a:b] = oracle.merge_sort_pairs(keys[a:b], vals[a:b], False)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(tk), wk) and np.array_equal(to_host(tv), wv)
+    else:
+        bt.sort_segmented_(tk, to, ascending=False)
+        for a, b in zip(offs[:-1], offs[1:]):
+            if b > a:
+                wk[a:b] = oracle.merge_sort(keys[a:b], False)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(tk), wk)
+
+
+@pytest.mark.parametrize("pairs", [False, True])
+def test_segmented_descending(pairs):
+    # edge lengths (empty, single, tile boundaries, longer than a tile) after
+    # 3 leading keys that lie outside every segment, then a mixed batch
+    lens = [0, 1, 2, 3, 0, 31, 32, 33, 4095, 4096, 4097, 8191, 8192, 8193, 16384, 16385, 40000, 0, 1, 5]
+    keys, offs = segments_case(lens, seed=13)
+    keys[:3] = np.uint32(0xFFFFFFFF)
+    check_segmented_descending(keys, offs, pairs)
+    keys, offs = workloads.segmented_u32(3000, seed=6, max_len=20000)
+    if pairs:  # many ties, so that the index order of equal keys is tested
+        keys = (keys >> np.uint32(24)).astype(np.uint32)
+    check_segmented_descending(keys, offs, pairs)
+
+
 def test_segmented_batched_workload():
     # 65,536 arrays, lengths log-uniform in [1, 8192]
     keys, offs = workloads.segmented_u32(65536, seed=workloads.SEEDS["segmented"])
