@@ -140,9 +140,10 @@ static uint32_t grid_for(uint32_t n)
 // 16-byte aligned (the composite workspace always is); the tail of fewer
 // than four elements is done element by element.
 __global__ void __launch_bounds__(256) k_pairs_pack4(ulonglong2* __restrict__ comp, const uint4* __restrict__ keys,
-                                                     uint32_t n4, uint32_t n, int desc,
-                                                     const uint32_t* __restrict__ keys1, uint64_t* __restrict__ comp1)
+                                                     uint32_t n4, uint32_t n, int desc)
 {
+    const uint32_t* keys1 = reinterpret_cast<const uint32_t*>(keys);  // element views for the tail
+    uint64_t* comp1 = reinterpret_cast<uint64_t*>(comp);
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
         uint4 k = keys[q];
         if (desc) {
@@ -160,8 +161,9 @@ __global__ void __launch_bounds__(256) k_pairs_pack4(ulonglong2* __restrict__ co
 }
 
 __global__ void __launch_bounds__(256) k_pairs_gather4(ulonglong2* __restrict__ comp, const uint32_t* __restrict__ vals,
-                                                       uint32_t n4, uint32_t n, uint64_t* __restrict__ comp1)
+                                                       uint32_t n4, uint32_t n)
 {
+    uint64_t* comp1 = reinterpret_cast<uint64_t*>(comp);  // element view for the tail
     constexpr uint64_t kHi = 0xFFFFFFFF00000000ull;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
         ulonglong2 a = comp[2 * q], b = comp[2 * q + 1];
@@ -180,10 +182,11 @@ __global__ void __launch_bounds__(256) k_pairs_gather4(ulonglong2* __restrict__ 
 }
 
 __global__ void __launch_bounds__(256) k_pairs_unpack4(const ulonglong2* __restrict__ comp, uint4* __restrict__ keys,
-                                                       uint4* __restrict__ vals, uint32_t n4, uint32_t n, int desc,
-                                                       const uint64_t* __restrict__ comp1, uint32_t* __restrict__ keys1,
-                                                       uint32_t* __restrict__ vals1)
+                                                       uint4* __restrict__ vals, uint32_t n4, uint32_t n, int desc)
 {
+    const uint64_t* comp1 = reinterpret_cast<const uint64_t*>(comp);  // element views for the tail
+    uint32_t* keys1 = reinterpret_cast<uint32_t*>(keys);
+    uint32_t* vals1 = reinterpret_cast<uint32_t*>(vals);
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
         const ulonglong2 a = comp[2 * q], b = comp[2 * q + 1];
         uint4 k = make_uint4((uint32_t)(a.x >> 32), (uint32_t)(a.y >> 32), (uint32_t)(b.x >> 32), (uint32_t)(b.y >> 32));
@@ -208,7 +211,7 @@ cudaError_t launch_pairs_pack(uint64_t* comp, const uint32_t* keys, uint32_t n, 
 {
     if (aligned16(keys) && aligned16(comp)) {
         const uint32_t n4 = n / 4;
-        k_pairs_pack4<<<grid_for(n4), 256, 0, s>>>((ulonglong2*)comp, (const uint4*)keys, n4, n, desc, keys, comp);
+        k_pairs_pack4<<<grid_for(n4), 256, 0, s>>>((ulonglong2*)comp, (const uint4*)keys, n4, n, desc);
     } else {
         k_pairs_pack<<<grid_for(n), 256, 0, s>>>(comp, keys, n, desc);
     }
@@ -219,7 +222,7 @@ cudaError_t launch_pairs_gather(uint64_t* comp, const uint32_t* vals, uint32_t n
 {
     if (aligned16(comp)) {
         const uint32_t n4 = n / 4;
-        k_pairs_gather4<<<grid_for(n4), 256, 0, s>>>((ulonglong2*)comp, vals, n4, n, comp);
+        k_pairs_gather4<<<grid_for(n4), 256, 0, s>>>((ulonglong2*)comp, vals, n4, n);
     } else {
         k_pairs_gather<<<grid_for(n), 256, 0, s>>>(comp, vals, n);
     }
@@ -232,7 +235,7 @@ cudaError_t launch_pairs_unpack(const uint64_t* comp, uint32_t* keys, uint32_t* 
     if (aligned16(comp) && aligned16(keys) && aligned16(vals)) {
         const uint32_t n4 = n / 4;
         k_pairs_unpack4<<<grid_for(n4), 256, 0, s>>>((const ulonglong2*)comp, (uint4*)keys, (uint4*)vals, n4, n,
-                                                     desc, comp, keys, vals);
+                                                     desc);
     } else {
         k_pairs_unpack<<<grid_for(n), 256, 0, s>>>(comp, keys, vals, n, desc);
     }
