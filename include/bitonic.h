@@ -249,6 +249,10 @@ typedef struct {
     int pipeline;         /* 0 = one CTA per tile (default); persistent CTAs that prefetch the
                              next tile into shared memory with 1 = TMA bulk copies per row,
                              2 = per-thread 16-byte cp.async copies */
+    int round_sync;       /* tile kernels: 0 = a shared-memory transpose after which every warp
+                             reads back exactly the slots it wrote waits at a warp barrier, the
+                             others at a CTA barrier (default); 1 = a CTA barrier after every
+                             transpose */
 } bitonic_options;
 
 /* Process-wide options (defaults: all zero except use_graph = 1 and l2_prefetch = 1). */

@@ -59,6 +59,10 @@ struct RoundDesc {
     uint8_t nsteps;
     uint8_t steps[kMaxStepsPerRound];
     uint8_t pattern;                   // index into the round-pattern catalog, 0xFF = generic
+    // 1 if every warp reads, in this round's layout, exactly the shared-memory
+    // slots it wrote in the previous round's layout: the transpose into this
+    // round then needs a warp barrier only, not a CTA barrier.
+    uint8_t warp_local;
     // Byte offsets of the 16-byte shared-memory vector slots, precomputed by
     // the planner: smem_swizzle(thr_loc[i] >> VB) * 16 and
     // smem_swizzle(reg_loc[j] >> VB) * 16.  By linearity a thread's vector v

@@ -59,6 +59,7 @@ struct Options {
     int min_row_log2 = 0;
     int ctas_per_sm = 0;
     int pipeline = 0;
+    int round_sync = 0;   // 0: warp barriers where a transpose keeps each warp's slots; 1: CTA barriers
 };
 
 // Builds the launch sequence for a sort of n keys of key_bytes bytes.

@@ -134,14 +134,21 @@ bool build_round(const std::vector<LStep>& steps, size_t i, size_t& j, int RR, i
     }
 }
 
-bool emit_round(const HostRound& hr, int log_t, int m, int vb, RoundDesc& rd)
+// Thread bits of a round: the local bits at or above vb that are not
+// register bits.
+std::vector<int> thread_bits(const HostRound& hr, int m, int vb)
 {
-    std::memset(&rd, 0, sizeof(rd));
     std::vector<int> T;
     for (int b = vb; b < m; ++b)
         if (!contains(hr.R, b)) T.push_back(b);
+    return T;
+}
+
+// Descriptor of round hr with thread-index bit i on local bit T[i].
+bool emit_round_ordered(const HostRound& hr, const std::vector<int>& T, int log_t, int m, int vb, RoundDesc& rd)
+{
+    std::memset(&rd, 0, sizeof(rd));
     if ((int)T.size() != log_t) return false;
-    T = order_thread_bits(T, vb);
     for (int t = 0; t < log_t; ++t) rd.thr_loc[t] = (uint16_t)(1u << T[t]);
     for (size_t q = 0; q < hr.R.size(); ++q) {
         uint32_t v = 1u << hr.R[q];
@@ -165,6 +172,11 @@ bool emit_round(const HostRound& hr, int log_t, int m, int vb, RoundDesc& rd)
         rd.steps[s] = (uint8_t)(q | (hr.steps[s].flip ? kStepFlip : 0));
     }
     return true;
+}
+
+bool emit_round(const HostRound& hr, int log_t, int m, int vb, RoundDesc& rd)
+{
+    return emit_round_ordered(hr, order_thread_bits(thread_bits(hr, m, vb), vb), log_t, m, vb, rd);
 }
 
 // Lanes 0..2 on local bits vb..vb+2 that the map sends to global units:
@@ -217,7 +229,116 @@ uint8_t find_pattern(const RoundDesc& rd, int log_r)
     return kGenericPattern;
 }
 
-bool plan_rounds(const std::vector<LStep>& steps, const TileCfg& cfg, int vb, int io_direct, TileParamsBig& P)
+// Lanes per warp: thread-index bits 0..4.
+constexpr int kLaneBits = 5;
+
+// Canonical form of the shared-memory slots one warp touches in a round's
+// layout: the reduced echelon basis of the span of the local vectors inside
+// a warp (vector components, register bits, lanes), followed by each warp
+// bit's local vector reduced modulo that span.  Two rounds with equal keys
+// give every warp the same set of local indices, hence of slots.
+std::vector<uint32_t> warp_key(const RoundDesc& rd, int log_t, int nreg, int vb)
+{
+    std::vector<uint32_t> basis;  // one vector per pivot (its highest bit), kept reduced
+    auto reduce = [&](uint32_t v) {
+        for (uint32_t b : basis) {
+            const uint32_t top = 1u << (31 - __builtin_clz(b));
+            if (v & top) v ^= b;
+        }
+        return v;
+    };
+    auto insert = [&](uint32_t v) {
+        v = reduce(v);
+        if (!v) return;
+        const uint32_t top = 1u << (31 - __builtin_clz(v));
+        for (uint32_t& b : basis)
+            if (b & top) b ^= v;
+        basis.push_back(v);
+        std::sort(basis.begin(), basis.end());
+    };
+    for (int c = 0; c < vb; ++c) insert(1u << c);
+    for (int j = 0; j < nreg; ++j) insert(rd.reg_loc[j]);
+    for (int t = 0; t < std::min(kLaneBits, log_t); ++t) insert(rd.thr_loc[t]);
+    std::vector<uint32_t> key = basis;
+    for (int t = kLaneBits; t < log_t; ++t) key.push_back(reduce(rd.thr_loc[t]) | 0x80000000u);
+    return key;
+}
+
+// Chooses every round's thread-bit order (which non-register bits are lanes
+// and which select the warp) so that as many transposes as possible keep
+// each warp's slots, then marks those rounds warp-local.  Lanes 0..2 keep
+// local bits of distinct residue mod 3 (conflict-free 16-byte shared
+// accesses); a first or last round that is coalesced stays coalesced.  A
+// dynamic program over the rounds: score 2 per warp-local transpose, 1 per
+// round left in its default order.
+bool choose_thread_orders(const std::vector<HostRound>& hrs, std::vector<RoundDesc>& out, const TileParamsBig& P,
+                          int log_t, int m, int vb, int nreg)
+{
+    const size_t nr = out.size();
+    if (nr < 2 || log_t <= kLaneBits) return true;
+    const int nwarp = log_t - kLaneBits;
+    struct Cand {
+        RoundDesc rd;
+        std::vector<uint32_t> key;
+        int score = 0;
+        int prev = -1;
+    };
+    std::vector<std::vector<Cand>> cands(nr);
+    for (size_t r = 0; r < nr; ++r) {
+        const std::vector<int> T = thread_bits(hrs[r], m, vb);
+        if ((int)T.size() != log_t) return false;
+        const bool keep_coalesced = (r == 0 || r + 1 == nr) && round_coalesced(out[r], P, vb);
+        Cand def;
+        def.rd = out[r];
+        def.key = warp_key(out[r], log_t, nreg, vb);
+        def.score = 1;
+        cands[r].push_back(def);
+        // every choice of the warp bits among the thread bits
+        const int nt = (int)T.size();
+        for (uint32_t sel = 0; sel < (1u << nt); ++sel) {
+            if (__builtin_popcount(sel) != nwarp) continue;
+            std::vector<int> lanes, warps;
+            for (int t = 0; t < nt; ++t) ((sel >> t) & 1u ? warps : lanes).push_back(T[t]);
+            std::vector<int> order = order_thread_bits(lanes, vb);
+            bool res[3] = {false, false, false};
+            for (int t = 0; t < 3; ++t) res[(order[t] - vb) % 3] = true;
+            if (!(res[0] && res[1] && res[2])) continue;
+            order.insert(order.end(), warps.begin(), warps.end());
+            Cand c;
+            if (!emit_round_ordered(hrs[r], order, log_t, m, vb, c.rd)) return false;
+            if (keep_coalesced && !round_coalesced(c.rd, P, vb)) continue;
+            if (std::memcmp(&c.rd, &out[r], sizeof(RoundDesc)) == 0) continue;  // the default
+            c.key = warp_key(c.rd, log_t, nreg, vb);
+            cands[r].push_back(c);
+        }
+    }
+    for (size_t r = 1; r < nr; ++r)
+        for (Cand& c : cands[r]) {
+            int best = -1, arg = -1;
+            for (size_t q = 0; q < cands[r - 1].size(); ++q) {
+                const Cand& p = cands[r - 1][q];
+                const int v = p.score + (p.key == c.key ? 2 : 0);
+                if (v > best) { best = v; arg = (int)q; }
+            }
+            c.score += best;
+            c.prev = arg;
+        }
+    int arg = 0;
+    for (size_t q = 1; q < cands[nr - 1].size(); ++q)
+        if (cands[nr - 1][q].score > cands[nr - 1][arg].score) arg = (int)q;
+    for (size_t r = nr; r-- > 0;) {
+        const Cand& c = cands[r][arg];
+        out[r] = c.rd;
+        if (r > 0) {
+            out[r].warp_local = cands[r - 1][c.prev].key == c.key ? 1 : 0;
+            arg = c.prev;
+        }
+    }
+    return true;
+}
+
+bool plan_rounds(const std::vector<LStep>& steps, const TileCfg& cfg, int vb, int io_direct, TileParamsBig& P,
+                 bool warp_sync = false)
 {
     const int m = cfg.log_r + cfg.log_t;
     const int RR = cfg.log_r - vb;
@@ -240,10 +361,18 @@ bool plan_rounds(const std::vector<LStep>& steps, const TileCfg& cfg, int vb, in
     // Global loads and stores go through a coalesced layout: add a round
     // without steps (one more shared-memory transpose) where needed.
     RoundDesc io;
-    if (!emit_round(io_round(RR, m, vb), cfg.log_t, m, vb, io)) return false;
-    if (!(io_direct & 1) && !round_coalesced(out.front(), P, vb)) out.insert(out.begin(), io);
-    if (!(io_direct & 2) && !round_coalesced(out.back(), P, vb)) out.push_back(io);
+    const HostRound ioh = io_round(RR, m, vb);
+    if (!emit_round(ioh, cfg.log_t, m, vb, io)) return false;
+    if (!(io_direct & 1) && !round_coalesced(out.front(), P, vb)) {
+        out.insert(out.begin(), io);
+        rounds.insert(rounds.begin(), ioh);
+    }
+    if (!(io_direct & 2) && !round_coalesced(out.back(), P, vb)) {
+        out.push_back(io);
+        rounds.push_back(ioh);
+    }
     if (out.size() > (size_t)kMaxRoundsBig) return false;
+    if (warp_sync && !choose_thread_orders(rounds, out, P, cfg.log_t, m, vb, RR)) return false;
     for (RoundDesc& rd : out) rd.pattern = find_pattern(rd, cfg.log_r);
     P.nrounds = (uint8_t)out.size();
     for (size_t r = 0; r < out.size(); ++r) P.rounds[r] = out[r];
@@ -371,7 +500,7 @@ bool make_class_desc(int key_bytes, int k, TileParamsBig& P)
     std::vector<int> B;
     for (int b = 0; b < m; ++b) B.push_back(b);
     if (!map_bits(P, B, false, m)) return false;
-    return plan_rounds(tile_sort_steps(k), cfg, vb, 0, P);
+    return plan_rounds(tile_sort_steps(k), cfg, vb, 0, P, true);
 }
 
 Plan make_plan(uint64_t nv, int key_bytes, const Options& opt)
@@ -401,6 +530,9 @@ Plan make_plan(uint64_t nv, int key_bytes, const Options& opt)
     const int c_min = opt.min_row_log2 ? std::max(vb + 1, opt.min_row_log2) : vb + 3;
     const bool semi = opt.variant == 2;
     const bool fuse = !semi;   // let a pass run across a phase boundary
+    // Transposes that keep every warp's slots wait at a warp barrier (the
+    // semi variant keeps a CTA barrier after every transpose).
+    const bool warp_sync = !semi && opt.round_sync == 0;
     // At most this many strides at or above the tile size per pass; 0 =
     // automatic: 8 (2^28 4-byte keys on GB300: 13.34 ms against 13.59 ms
     // uncapped, the cost-based split then preferring 2-round passes).
@@ -414,7 +546,7 @@ Plan make_plan(uint64_t nv, int key_bytes, const Options& opt)
         TileParamsBig P;
         std::memset(&P, 0, sizeof(P));
         if (!map_bits(P, B, affine, k)) return false;
-        if (!plan_rounds(ls, cfg, vb, opt.io_direct, P)) return false;
+        if (!plan_rounds(ls, cfg, vb, opt.io_direct, P, warp_sync)) return false;
         TileParams small;
         const bool fits = to_small(P, small);
         plan.descs.push_back(P);

@@ -142,9 +142,9 @@ k_seg_tiles(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const int3
         steps_in_place<kCat, false>(tl.r, r0);
         const int nr = P.nrounds;
         for (int rd = 1; rd < nr; ++rd) {
-            if (rd > 1) __syncthreads();
+            // the write goes to the slots this thread read last round (no barrier)
             tl.smem_write(sm, P.rounds[rd - 1], x);
-            __syncthreads();
+            round_barrier(P.rounds[rd]);
             tl.smem_read(sm, P.rounds[rd], x);
             steps_in_place<kCat, false>(tl.r, P.rounds[rd]);
         }

@@ -42,7 +42,9 @@ __device__ __forceinline__ void steps_in_place(K (&r)[R], const RoundDesc& rd)
 }
 
 // A middle round: shared-memory read, steps, shared-memory write, with the
-// registers local to the round.
+// registers local to the round.  The write goes back to the slots this
+// thread has just read (the same layout), so it needs no barrier: no other
+// thread reads or writes those slots in this round.
 template <typename K, bool DESC, int LOG_R, int LOG_T, bool CATALOG, int I = 0>
 __device__ __forceinline__ void middle_round(typename Tile<K, DESC, LOG_R, LOG_T>::Vec* sm, const RoundDesc& rd,
                                              uint32_t x)
@@ -53,7 +55,6 @@ __device__ __forceinline__ void middle_round(typename Tile<K, DESC, LOG_R, LOG_T
             T u;
             u.smem_read(sm, rd, x);
             pattern_steps<LOG_R, I, 0, DESC>(u.r);
-            __syncthreads();
             u.smem_write(sm, rd, x);
             return;
         }
@@ -62,9 +63,20 @@ __device__ __forceinline__ void middle_round(typename Tile<K, DESC, LOG_R, LOG_T
         T u;
         u.smem_read(sm, rd, x);
         run_round_steps<DESC>(u.r, rd);
-        __syncthreads();
         u.smem_write(sm, rd, x);
     }
+}
+
+// Orders the previous round's shared-memory writes before this round's
+// reads: a warp barrier where the planner marked the transpose warp-local
+// (every warp reads back exactly the slots it wrote), else a CTA barrier.
+// The flag is the same for every thread of the CTA.
+__device__ __forceinline__ void round_barrier(const RoundDesc& rd)
+{
+    if (rd.warp_local)
+        __syncwarp();
+    else
+        __syncthreads();
 }
 
 // The rounds of one tile once round 0's keys are in t's registers: round 0's
@@ -82,10 +94,10 @@ __device__ __forceinline__ void run_tile_rounds(Tile<K, DESC, LOG_R, LOG_T>& t,
     if (nr > 1) {
         t.smem_write(sm, P.rounds[0], x);
         for (int rd = 1; rd < nr - 1; ++rd) {
-            __syncthreads();
+            round_barrier(P.rounds[rd]);
             middle_round<K, DESC, LOG_R, LOG_T, CATALOG>(sm, P.rounds[rd], x);
         }
-        __syncthreads();
+        round_barrier(P.rounds[nr - 1]);
         t.smem_read(sm, P.rounds[nr - 1], x);
         steps_in_place<kCat, DESC>(t.r, P.rounds[nr - 1]);
     }

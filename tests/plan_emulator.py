@@ -44,6 +44,8 @@ class Stats:
         self.conflicted_quarter_warps = 0
         self.quarter_warps = 0
         self.uncoalesced_rounds = 0
+        self.transposes = 0
+        self.warp_local_transposes = 0
 
 
 def _round_local(rd, log_r, log_t, vb):
@@ -141,6 +143,16 @@ def emulate(keys: np.ndarray, ascending: bool = True, front: int = 0, stats: Sta
             slot = (_xor_span(rd["thr_sw"], log_t)[:, None]
                     ^ _xor_span(rd["reg_sw"], log_r - vb)[None, :])
             assert np.array_equal(slot, _swz(Lr[:, ::(1 << vb)] >> vb) << 4), "shared-memory slots"
+        # a transpose marked warp-local waits at a warp barrier only: every
+        # warp must read, in the new layout, exactly the local indices (hence
+        # shared-memory slots) it wrote in the previous one
+        for r in range(1, nr):
+            stats.transposes += 1
+            if int(rounds[r]["warp_local"]):
+                stats.warp_local_transposes += 1
+                a_w = np.sort(layouts[r - 1].reshape(-1, 32 * (1 << log_r)), axis=1)
+                b_w = np.sort(layouts[r].reshape(-1, 32 * (1 << log_r)), axis=1)
+                assert np.array_equal(a_w, b_w), "warp-local transpose moves keys between warps"
         for idx in (0, nr - 1):
             thr = rounds[idx]["thr_loc"]
             need = min(3, c - vb)
