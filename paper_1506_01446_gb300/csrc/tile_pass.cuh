@@ -20,7 +20,10 @@ __device__ __forceinline__ void pattern_steps(K (&r)[R])
     constexpr RoundPattern p = catalog_pattern(LOG_R, IDX);
     if constexpr (S < p.n) {
         constexpr int code = p.steps[S];
-        net_step<code & 15, (code & kStepFlip) != 0, DESC>(r);
+        if constexpr ((code & kStepLane) != 0)
+            lane_step<code & 7, (code & kStepFlip) != 0, DESC>(r);
+        else
+            net_step<code & 15, (code & kStepFlip) != 0, DESC>(r);
         pattern_steps<LOG_R, IDX, S + 1, DESC>(r);
     }
 }
