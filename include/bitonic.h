@@ -253,10 +253,6 @@ typedef struct {
                              reads back exactly the slots it wrote waits at a warp barrier, the
                              others at a CTA barrier (default); 1 = a CTA barrier after every
                              transpose */
-    int shuffle;          /* tile kernels: 1 = the tile sort runs its phases whose steps stay
-                             inside a warp in one round, the steps on lane bits as
-                             __shfl_xor_sync exchanges instead of shared-memory transposes;
-                             0 = off (default) */
 } bitonic_options;
 
 /* Process-wide options (defaults: all zero except use_graph = 1 and l2_prefetch = 1). */

@@ -51,7 +51,7 @@ class Options(ctypes.Structure):
                 ("global_bits", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("keys_per_thread_log2", ctypes.c_int), ("io_direct", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("min_row_log2", ctypes.c_int), ("l2_prefetch", ctypes.c_int),
-                ("pipeline", ctypes.c_int), ("round_sync", ctypes.c_int), ("shuffle", ctypes.c_int)]
+                ("pipeline", ctypes.c_int), ("round_sync", ctypes.c_int)]
 
 
 _lib = None
@@ -272,13 +272,12 @@ def get_options() -> dict:
 
 def set_options(variant=None, tile_log2=None, global_bits=None, use_graph=None,
                 keys_per_thread_log2=None, io_direct=None, pipeline=None, l2_prefetch=None,
-                min_row_log2=None, ctas_per_sm=None, round_sync=None, shuffle=None):
+                min_row_log2=None, ctas_per_sm=None, round_sync=None):
     cur = get_options()
     for k, v in (("variant", variant), ("tile_log2", tile_log2), ("global_bits", global_bits),
                  ("use_graph", use_graph), ("keys_per_thread_log2", keys_per_thread_log2),
                  ("io_direct", io_direct), ("pipeline", pipeline), ("l2_prefetch", l2_prefetch),
-                 ("min_row_log2", min_row_log2), ("ctas_per_sm", ctas_per_sm), ("round_sync", round_sync),
-                 ("shuffle", shuffle)):
+                 ("min_row_log2", min_row_log2), ("ctas_per_sm", ctas_per_sm), ("round_sync", round_sync)):
         if v is not None:
             cur[k] = int(v)
     _check(load().bitonic_set_options(ctypes.byref(Options(**cur))), "bitonic_set_options")
@@ -305,7 +304,7 @@ def desc_dtype():
     """numpy layout of one launch descriptor (TileParamsBig in csrc/desc.h)."""
     import numpy as np
     rnd = np.dtype([("thr_loc", "<u2", 10), ("reg_loc", "<u2", 5), ("nsteps", "u1"),
-                    ("steps", "u1", 72), ("pattern", "u1"), ("warp_local", "u1"), ("pad_r", "u1"),
+                    ("steps", "u1", 36), ("pattern", "u1"), ("warp_local", "u1"), ("pad_r", "u1"),
                     ("thr_sw", "<u2", 10), ("reg_sw", "<u2", 5)])
     io = np.dtype([("thr_glob", "<u4", 10), ("reg_glob", "<u4", 5)])
     return np.dtype([("gvec", "<u4", 16), ("io", io, 2), ("span_mask", "<u4"), ("run_shift", "u1", 4),

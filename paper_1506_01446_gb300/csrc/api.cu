@@ -88,7 +88,7 @@ Options resolve_options(int key_bytes, int k)
 uint64_t options_code(const Options& o)
 {
     const int f[] = {o.variant, o.tile_log2, o.keys_per_thread_log2, o.global_bits, o.io_direct,
-                     o.pipeline, o.l2_prefetch, o.min_row_log2, o.ctas_per_sm, o.round_sync, o.shuffle};
+                     o.pipeline, o.l2_prefetch, o.min_row_log2, o.ctas_per_sm, o.round_sync};
     uint64_t c = 0;
     for (int v : f) c = (c << 5) | uint64_t(v & 31);
     return c;
@@ -1001,7 +1001,6 @@ bitonic_status bitonic_set_options(const bitonic_options* opt)
     g_opt.min_row_log2 = (opt->min_row_log2 < 0 || opt->min_row_log2 > 12) ? 0 : opt->min_row_log2;
     g_opt.ctas_per_sm = (opt->ctas_per_sm == 2 || opt->ctas_per_sm == 3) ? opt->ctas_per_sm : 0;
     g_opt.round_sync = opt->round_sync ? 1 : 0;
-    g_opt.shuffle = opt->shuffle ? 1 : 0;
     return BITONIC_OK;
 }
 
@@ -1054,7 +1053,6 @@ bitonic_status bitonic_get_options(bitonic_options* opt)
     opt->min_row_log2 = g_opt.min_row_log2;
     opt->ctas_per_sm = g_opt.ctas_per_sm;
     opt->round_sync = g_opt.round_sync;
-    opt->shuffle = g_opt.shuffle;
     return BITONIC_OK;
 }
 

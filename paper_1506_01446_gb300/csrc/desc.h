@@ -30,16 +30,12 @@ constexpr int kMaxLogThreads = 10;
 constexpr int kMaxRegBits = 5;        // LOG_R - VB
 constexpr int kMaxRoundsSmall = 32;   // descriptors passed by value (constant bank)
 constexpr int kMaxRoundsBig = 100;    // descriptors read from global memory
-constexpr int kMaxStepsPerRound = 72;
+constexpr int kMaxStepsPerRound = 36;
 constexpr int kMaxLocalBits = 16;
 constexpr int kMaxCtaRuns = 4;
 
 // Step code: register-index bit q in bits 0..3, kStepFlip set for a mirror step.
-// With kStepLane set, bits 0..2 name a lane bit L instead: the step's partner
-// is in lane ^ 2^L (half-cleaner) or lane ^ (2^(L+1) - 1) with the register
-// order reversed (mirror step), reached by a warp shuffle.
 constexpr uint8_t kStepFlip = 16;
-constexpr uint8_t kStepLane = 64;
 
 #if defined(__CUDACC__)
 #define BITONIC_HD __host__ __device__

@@ -83,40 +83,6 @@ __device__ __forceinline__ void net_step(K (&r)[R])
     }
 }
 
-// One network step whose bit is lane bit L of the round's layout (the
-// shuffle form of Section 4.2's register steps): each key meets its partner
-// in lane ^ 2^L (half-cleaner), or in lane ^ (2^(L+1) - 1) at the mirrored
-// register (mirror step; the planner emits it only when every register bit
-// lies below the step's bit), through __shfl_xor_sync.  The thread whose lane
-// bit L is clear holds the lower position and keeps the key that sorts
-// first.  Lanes are the low five bits of the thread index.
-template <int L, bool FLIP, bool DESC, typename K, int R>
-__device__ __forceinline__ void lane_step(K (&r)[R])
-{
-    constexpr int kMask = FLIP ? ((2 << L) - 1) : (1 << L);
-    const bool keep_hi = (((threadIdx.x >> L) & 1u) != 0) != DESC;
-    if constexpr (!FLIP) {
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const K y = __shfl_xor_sync(0xFFFFFFFFu, r[i], kMask);
-            const K lo = r[i] < y ? r[i] : y;
-            const K hi = r[i] < y ? y : r[i];
-            r[i] = keep_hi ? hi : lo;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < R / 2; ++i) {
-            const int j = R - 1 - i;
-            const K yi = __shfl_xor_sync(0xFFFFFFFFu, r[j], kMask);
-            const K yj = __shfl_xor_sync(0xFFFFFFFFu, r[i], kMask);
-            const K loi = r[i] < yi ? r[i] : yi, hii = r[i] < yi ? yi : r[i];
-            const K loj = r[j] < yj ? r[j] : yj, hij = r[j] < yj ? yj : r[j];
-            r[i] = keep_hi ? hii : loi;
-            r[j] = keep_hi ? hij : loj;
-        }
-    }
-}
-
 template <bool DESC, typename K, int R>
 __device__ __forceinline__ void run_step(K (&r)[R], int code)
 {
@@ -136,19 +102,6 @@ __device__ __forceinline__ void run_step(K (&r)[R], int code)
         BITONIC_STEP_CASE(4)
         BITONIC_STEP_CASE(5)
         BITONIC_STEP_CASE(6)
-#define BITONIC_LANE_CASE(L)                                                  \
-    case kStepLane + L:                                                       \
-        lane_step<L, false, DESC>(r);                                         \
-        break;                                                                \
-    case kStepLane + kStepFlip + L:                                           \
-        lane_step<L, true, DESC>(r);                                          \
-        break;
-        BITONIC_LANE_CASE(0)
-        BITONIC_LANE_CASE(1)
-        BITONIC_LANE_CASE(2)
-        BITONIC_LANE_CASE(3)
-        BITONIC_LANE_CASE(4)
-#undef BITONIC_LANE_CASE
         default: break;
     }
 #undef BITONIC_STEP_CASE

@@ -60,7 +60,6 @@ struct Options {
     int ctas_per_sm = 0;
     int pipeline = 0;
     int round_sync = 0;   // 0: warp barriers where a transpose keeps each warp's slots; 1: CTA barriers
-    int shuffle = 0;      // 1: the tile sort's phases below the warp run in one round with shuffle steps
 };
 
 // Builds the launch sequence for a sort of n keys of key_bytes bytes.

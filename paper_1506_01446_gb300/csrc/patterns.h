@@ -14,7 +14,7 @@
 
 namespace bitonic {
 
-constexpr int kMaxPatternSteps = kMaxStepsPerRound;
+constexpr int kMaxPatternSteps = 28;
 constexpr uint8_t kGenericPattern = 0xFF;
 
 struct RoundPattern {
@@ -28,20 +28,12 @@ struct PatternSpec {
     int s, a, b, f, c;
 };
 
-// Code of a step at register-index bit b of a thread with 2^log_r keys;
-// bits from log_r up are lane bits (lane b - log_r, a shuffle step).
-constexpr uint8_t bit_code(int b, int log_r, bool flip)
-{
-    const int c = b < log_r ? b : (kStepLane | (b - log_r));
-    return (uint8_t)(c | (flip ? kStepFlip : 0));
-}
-
-constexpr RoundPattern build_pattern(PatternSpec p, int log_r)
+constexpr RoundPattern build_pattern(PatternSpec p)
 {
     RoundPattern r{0, {}};
     for (int q = 1; q <= p.s; ++q) {
-        r.steps[r.n++] = bit_code(q - 1, log_r, true);
-        for (int h = q - 2; h >= 0; --h) r.steps[r.n++] = bit_code(h, log_r, false);
+        r.steps[r.n++] = (uint8_t)((q - 1) | kStepFlip);
+        for (int h = q - 2; h >= 0; --h) r.steps[r.n++] = (uint8_t)h;
     }
     if (p.a >= 0)
         for (int h = p.a; h >= p.b; --h) r.steps[r.n++] = (uint8_t)h;
@@ -62,7 +54,6 @@ constexpr PatternSpec kCatalogR6[] = {
     {0, -1, 0, 5, 2}, {0, -1, 0, 5, 3}, {0, -1, 0, 5, 4}, {0, -1, 0, 5, 5},
     {0, 2, 0, 5, 3}, {0, 3, 0, 5, 4}, {0, 4, 0, 5, 5}, {0, 2, 0, 5, 2},
     {6, -1, 0, -1, 0}, {5, -1, 0, -1, 0},
-    {11, -1, 0, -1, 0},  // phases 1..11: register bits 0..5, then lanes 0..4 (shuffle steps)
 };
 constexpr PatternSpec kCatalogR5[] = {
     {0, -1, 0, -1, 0},
@@ -71,7 +62,6 @@ constexpr PatternSpec kCatalogR5[] = {
     {0, -1, 0, 4, 1}, {0, -1, 0, 4, 2}, {0, -1, 0, 4, 3}, {0, -1, 0, 4, 4},
     {0, 1, 0, 4, 2}, {0, 2, 0, 4, 3}, {0, 3, 0, 4, 4}, {0, 2, 0, 4, 4}, {0, 1, 0, 4, 1},
     {5, -1, 0, -1, 0}, {4, -1, 0, -1, 0},
-    {10, -1, 0, -1, 0},  // phases 1..10: register bits 0..4, then lanes 0..4 (shuffle steps)
 };
 constexpr int kCatalogR6Size = sizeof(kCatalogR6) / sizeof(kCatalogR6[0]);
 constexpr int kCatalogR5Size = sizeof(kCatalogR5) / sizeof(kCatalogR5[0]);
@@ -84,6 +74,6 @@ constexpr PatternSpec catalog_spec(int log_r, int i)
     return log_r == 6 ? kCatalogR6[i] : kCatalogR5[i];
 }
 
-constexpr RoundPattern catalog_pattern(int log_r, int i) { return build_pattern(catalog_spec(log_r, i), log_r); }
+constexpr RoundPattern catalog_pattern(int log_r, int i) { return build_pattern(catalog_spec(log_r, i)); }
 
 }  // namespace bitonic

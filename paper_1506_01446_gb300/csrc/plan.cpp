@@ -82,29 +82,7 @@ struct HostRound {
     std::vector<LStep> steps;
     int mirror_bit = -1;         // register bit carrying thread components
     uint32_t mirror = 0;
-    std::vector<int> lanes;      // shuffle round: local bit of lane bit i (its steps there are lane steps)
 };
-
-// Lanes per warp: thread-index bits 0..4.
-constexpr int kLaneBits = 5;
-
-// A shuffle round from step i: registers hold local bits vb..vb+RR-1, lanes
-// the next five bits, and the round takes every following step whose bit is
-// below those (the tile sort's phases 1..vb+RR+5).  Steps on lane bits run as
-// warp shuffles; a mirror step on a lane bit has every register bit below
-// it, so its partner is the mirrored register of the mirrored lane.
-bool build_lane_round(const std::vector<LStep>& steps, size_t i, size_t& j, int RR, int m, int vb, HostRound& hr)
-{
-    const int top = vb + RR + kLaneBits;
-    if (top > m) return false;
-    hr = HostRound();
-    for (int b = vb; b < vb + RR; ++b) hr.R.push_back(b);
-    for (int b = vb + RR; b < top; ++b) hr.lanes.push_back(b);
-    j = i;
-    while (j < steps.size() && steps[j].bit < top && j - i < (size_t)kMaxStepsPerRound) ++j;
-    hr.steps.assign(steps.begin() + i, steps.begin() + j);
-    return j > i;
-}
 
 void fill_registers(std::vector<int>& R, int RR, int m, int vb)
 {
@@ -157,12 +135,12 @@ bool build_round(const std::vector<LStep>& steps, size_t i, size_t& j, int RR, i
 }
 
 // Thread bits of a round: the local bits at or above vb that are not
-// register bits (a shuffle round's lanes first, in lane order).
+// register bits.
 std::vector<int> thread_bits(const HostRound& hr, int m, int vb)
 {
-    std::vector<int> T = hr.lanes;
+    std::vector<int> T;
     for (int b = vb; b < m; ++b)
-        if (!contains(hr.R, b) && !contains(hr.lanes, b)) T.push_back(b);
+        if (!contains(hr.R, b)) T.push_back(b);
     return T;
 }
 
@@ -188,8 +166,6 @@ bool emit_round_ordered(const HostRound& hr, const std::vector<int>& T, int log_
         int q;
         if (b < vb) {
             q = b;
-        } else if (contains(hr.lanes, b)) {
-            q = kStepLane | (int)(std::find(hr.lanes.begin(), hr.lanes.end(), b) - hr.lanes.begin());
         } else {
             q = vb + (int)(std::find(hr.R.begin(), hr.R.end(), b) - hr.R.begin());
         }
@@ -200,8 +176,7 @@ bool emit_round_ordered(const HostRound& hr, const std::vector<int>& T, int log_
 
 bool emit_round(const HostRound& hr, int log_t, int m, int vb, RoundDesc& rd)
 {
-    const std::vector<int> T = thread_bits(hr, m, vb);
-    return emit_round_ordered(hr, hr.lanes.empty() ? order_thread_bits(T, vb) : T, log_t, m, vb, rd);
+    return emit_round_ordered(hr, order_thread_bits(thread_bits(hr, m, vb), vb), log_t, m, vb, rd);
 }
 
 // Lanes 0..2 on local bits vb..vb+2 that the map sends to global units:
@@ -253,6 +228,9 @@ uint8_t find_pattern(const RoundDesc& rd, int log_r)
     }
     return kGenericPattern;
 }
+
+// Lanes per warp: thread-index bits 0..4.
+constexpr int kLaneBits = 5;
 
 // Canonical form of the shared-memory slots one warp touches in a round's
 // layout: the reduced echelon basis of the span of the local vectors inside
@@ -315,7 +293,6 @@ bool choose_thread_orders(const std::vector<HostRound>& hrs, std::vector<RoundDe
         def.key = warp_key(out[r], log_t, nreg, vb);
         def.score = 1;
         cands[r].push_back(def);
-        if (!hrs[r].lanes.empty()) continue;  // a shuffle round's lanes are fixed
         // every choice of the warp bits among the thread bits
         const int nt = (int)T.size();
         for (uint32_t sel = 0; sel < (1u << nt); ++sel) {
@@ -361,22 +338,15 @@ bool choose_thread_orders(const std::vector<HostRound>& hrs, std::vector<RoundDe
 }
 
 bool plan_rounds(const std::vector<LStep>& steps, const TileCfg& cfg, int vb, int io_direct, TileParamsBig& P,
-                 bool warp_sync = false, bool lane_round = false)
+                 bool warp_sync = false)
 {
     const int m = cfg.log_r + cfg.log_t;
     const int RR = cfg.log_r - vb;
     std::vector<HostRound> rounds;
     size_t i = 0;
-    // A tile sort (phase 1 first) may open with a shuffle round.
-    const bool lanes = lane_round && !steps.empty() && steps[0].bit == 0 && steps[0].flip;
     while (i < steps.size()) {
         size_t j;
         HostRound hr;
-        if (lanes && i == 0 && build_lane_round(steps, i, j, RR, m, vb, hr)) {
-            rounds.push_back(hr);
-            i = j;
-            continue;
-        }
         if (!build_round(steps, i, j, RR, m, vb, hr)) return false;
         rounds.push_back(hr);
         i = j;
@@ -576,7 +546,7 @@ Plan make_plan(uint64_t nv, int key_bytes, const Options& opt)
         TileParamsBig P;
         std::memset(&P, 0, sizeof(P));
         if (!map_bits(P, B, affine, k)) return false;
-        if (!plan_rounds(ls, cfg, vb, opt.io_direct, P, warp_sync, !semi && opt.shuffle != 0)) return false;
+        if (!plan_rounds(ls, cfg, vb, opt.io_direct, P, warp_sync)) return false;
         TileParams small;
         const bool fits = to_small(P, small);
         plan.descs.push_back(P);

@@ -20,10 +20,7 @@ __device__ __forceinline__ void pattern_steps(K (&r)[R])
     constexpr RoundPattern p = catalog_pattern(LOG_R, IDX);
     if constexpr (S < p.n) {
         constexpr int code = p.steps[S];
-        if constexpr ((code & kStepLane) != 0)
-            lane_step<code & 7, (code & kStepFlip) != 0, DESC>(r);
-        else
-            net_step<code & 15, (code & kStepFlip) != 0, DESC>(r);
+        net_step<code & 15, (code & kStepFlip) != 0, DESC>(r);
         pattern_steps<LOG_R, IDX, S + 1, DESC>(r);
     }
 }

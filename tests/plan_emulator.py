@@ -74,19 +74,6 @@ def _check_banks(Lr, vb, stats):
 def _apply_steps(regs, steps, desc):
     R = regs.shape[-1]
     for code in steps:
-        if code & 64:
-            # lane step: partner in lane ^ 2^L (or lane ^ (2^(L+1) - 1) with the
-            # registers mirrored); the thread whose lane bit L is clear keeps
-            # the key that sorts first
-            L, flip = code & 7, bool(code & 16)
-            x = np.arange(regs.shape[1])
-            mask = ((2 << L) - 1) if flip else (1 << L)
-            y = regs[:, x ^ mask, :]
-            if flip:
-                y = y[..., ::-1]
-            keep_hi = (((x >> L) & 1).astype(bool) != desc)[None, :, None]
-            regs[...] = np.where(keep_hi, np.maximum(regs, y), np.minimum(regs, y))
-            continue
         q, flip = code & 15, bool(code & 16)
         i = np.array([r for r in range(R) if not (r >> q) & 1])
         j = (i ^ ((2 << q) - 1)) if flip else (i | (1 << q))
