@@ -315,9 +315,19 @@ KeyMaps key_maps(int type, int ascending)
     return m;
 }
 
+// Pair sorts build their composites in the first tile launch and split them
+// in the last one (PairIo) when the plan runs on tile kernels of a composite
+// configuration that has those kernels, with by-value descriptors; otherwise
+// separate pack, gather and split kernels surround the plan.
+bool pairs_fused(const Plan& pl, const Options& o)
+{
+    return !pl.launches.empty() && pl.launches[0].kind != KIND_STEP && !o.pipeline && tile_pairs_supported(pl.cfg) &&
+           pl.launches.front().small && pl.launches.back().small;
+}
+
 bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* base, uint32_t lo, uint32_t hi,
                             const KeyMaps& km, int key_bytes, int* status, cudaStream_t s, cudaEvent_t* events,
-                            int* kinds)
+                            int* kinds, const PairIo* pio = nullptr)
 {
     const Plan& pl = pe.plan;
     const uint64_t ones = key_bytes == 8 ? ~0ull : 0xFFFFFFFFull;
@@ -361,7 +371,13 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
             // The key maps are fused into the first load and the last store.
             const KeyMapHost& mi = (i == 0 && !separate) ? km.in : ident;
             const KeyMapHost& mo = (i + 1 == pl.launches.size() && !separate) ? km.out : ident;
-            if (piped) {
+            const int pmode = pio ? ((i == 0 ? 1 : 0) | (i + 1 == pl.launches.size() ? 2 : 0)) : 0;
+            if (pmode) {
+                const uint32_t pf = (pmode == 2 && pe.opt.l2_prefetch > 0)
+                                        ? (uint32_t)(pe.opt.l2_prefetch * ds.tile_blocks[pl.cfg] * ds.num_sms)
+                                        : 0u;
+                e = launch_tile_pairs(pl.cfg, pmode, (uint64_t*)base, hi, hP, ntiles, *pio, pf, s);
+            } else if (piped) {
                 const int per_sm = ds.pipe_blocks[pl.cfg];
                 uint64_t g = (uint64_t)per_sm * ds.num_sms;
                 const uint32_t grid = (uint32_t)(g < ntiles ? g : ntiles);
@@ -711,15 +727,40 @@ bitonic_status sort_pairs_impl(uint32_t* keys, uint32_t* vals, size_t n, int asc
     std::lock_guard<std::mutex> g(g_mu);
     DeviceState* ds;
     if ((st = device_state(&ds))) return st;
-    StreamWs* w;
-    if ((st = stream_ws(*ds, s, n, &w))) return st;
     PlanEntry* pe;
     if ((st = get_plan(*ds, n, 8, &pe))) return st;
+    const bool fused = pairs_fused(pe->plan, pe->opt);
+    // composites (n, rounded to 16 bytes), then, for the fused kernels, a
+    // copy of the values that the last launch gathers from
+    const size_t comp_elems = (n + 1) & ~size_t(1);
+    StreamWs* w;
+    if ((st = stream_ws(*ds, s, fused ? comp_elems + ((n + 3) / 4) * 2 : n, &w))) return st;
     const int desc = ascending ? 0 : 1;
     const uint32_t nn = (uint32_t)n;
     uint64_t* comp = w->comp;
     GraphKey key{1, n, desc, (uintptr_t)keys, (uintptr_t)vals, (uintptr_t)comp, 0, (uintptr_t)s, 0,
                  options_code(pe->opt), 0};
+    if (fused) {
+        // The last tile launch leaves the original indices after the
+        // composites; the values are gathered by index into the composite
+        // array (dead by then) and copied back over the caller's values.
+        uint32_t* idx = reinterpret_cast<uint32_t*>(comp + comp_elems);
+        uint32_t* vtmp = reinterpret_cast<uint32_t*>(comp);
+        PairIo pio;
+        pio.keys_in = keys;
+        pio.keys_out = keys;
+        pio.idx_out = idx;
+        pio.flip = desc ? 0xFFFFFFFFu : 0u;
+        pio.aligned8 = ((uintptr_t)keys & 7u) == 0 ? 1u : 0u;
+        return run_graphed(*ds, key, s, [&](cudaStream_t cs) -> bitonic_status {
+            bitonic_status st2 = enqueue_plan(*ds, *pe, comp, 0, nn, KeyMaps{}, 8, ds->status, cs, nullptr, nullptr,
+                                              &pio);
+            if (st2) return st2;
+            BT_CK(launch_gather_by_index(vtmp, vals, idx, nn, cs));
+            BT_CK(cudaMemcpyAsync(vals, vtmp, (size_t)nn * sizeof(uint32_t), cudaMemcpyDeviceToDevice, cs));
+            return BITONIC_OK;
+        });
+    }
     return run_graphed(*ds, key, s, [&](cudaStream_t cs) -> bitonic_status {
         BT_CK(launch_pairs_pack(comp, keys, nn, desc, cs));
         bitonic_status st2 = enqueue_plan(*ds, *pe, comp, 0, nn, KeyMaps{}, 8, ds->status, cs, nullptr, nullptr);
@@ -1077,7 +1118,7 @@ bitonic_status bitonic_plan_info(size_t n, int pairs, int* launches, int* hbm_pa
     }
     Plan p = make_plan(n, pairs ? 8 : 4, o);
     if (!p.ok) return BITONIC_ERR_UNSUPPORTED;
-    if (launches) *launches = (int)p.launches.size() + (pairs ? 3 : 0);
+    if (launches) *launches = (int)p.launches.size() + (pairs ? (pairs_fused(p, o) ? 1 : 3) : 0);
     if (hbm_passes) *hbm_passes = p.hbm_passes;
     if (fused_steps) *fused_steps = p.fused_steps;
     if (global_steps) *global_steps = p.global_steps;

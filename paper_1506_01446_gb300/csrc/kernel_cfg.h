@@ -76,4 +76,27 @@ cudaError_t init_pipe_attributes(int* blocks_per_sm);
 cudaError_t launch_step(int key_bytes, int desc, void* base, uint32_t lo, uint32_t hi, uint32_t N, int j,
                         int flip, cudaStream_t s);
 
+// Pair sorts on 64-bit composites (key' << 32) | index, key' = key ^ flip.
+// The first tile launch builds the composites while it loads the caller's
+// keys; the last one splits them while it stores: keys to keys_out, original
+// indices to idx_out.
+struct PairIo {
+    const uint32_t* keys_in;
+    uint32_t* keys_out;
+    uint32_t* idx_out;    // n indices, 16-byte aligned (workspace)
+    uint32_t flip;        // 0 ascending, all ones descending
+    uint32_t aligned8;    // keys 8-byte aligned: two-element vector accesses
+};
+
+// Composite tile configurations that have the fused pair kernels.
+bool tile_pairs_supported(int cfg);
+// mode bit 0: build composites on load; bit 1: split on store.  The launch
+// covers composites [0, hi) (no front padding).
+cudaError_t launch_tile_pairs(int cfg, int mode, uint64_t* comp, uint32_t hi, const TileParams* hP, uint32_t grid,
+                              const PairIo& pio, uint32_t pf_dist, cudaStream_t s);
+cudaError_t init_tile_pairs_attributes();
+// out[i] = vals[idx[i]] for i < n (out and idx 16-byte aligned).
+cudaError_t launch_gather_by_index(uint32_t* out, const uint32_t* vals, const uint32_t* idx, uint32_t n,
+                                   cudaStream_t s);
+
 }  // namespace bitonic

@@ -115,6 +115,7 @@ cudaError_t init_tile_attributes()
 {
     cudaError_t e = init_tile_attributes_u32();
     if (e == cudaSuccess) e = init_tile_attributes_u64();
+    if (e == cudaSuccess) e = init_tile_pairs_attributes();
     return e;
 }
 
@@ -205,7 +206,32 @@ __global__ void __launch_bounds__(256) k_pairs_unpack4(const ulonglong2* __restr
         }
 }
 
+// out[i] = vals[idx[i]]: four indices per thread as one 16-byte vector, the
+// four value reads issued independently, the results written as one vector.
+__global__ void __launch_bounds__(256) k_gather_by_index4(uint4* __restrict__ out, const uint32_t* __restrict__ vals,
+                                                          const uint4* __restrict__ idx, uint32_t n4, uint32_t n)
+{
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
+        const uint4 i = idx[q];
+        out[q] = make_uint4(vals[i.x], vals[i.y], vals[i.z], vals[i.w]);
+    }
+    if (blockIdx.x == 0) {
+        const uint32_t* idx1 = reinterpret_cast<const uint32_t*>(idx);
+        uint32_t* out1 = reinterpret_cast<uint32_t*>(out);
+        for (uint32_t i = 4 * n4 + threadIdx.x; i < n; i += blockDim.x) out1[i] = vals[idx1[i]];
+    }
+}
+
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+cudaError_t launch_gather_by_index(uint32_t* out, const uint32_t* vals, const uint32_t* idx, uint32_t n,
+                                   cudaStream_t s)
+{
+    if (!aligned16(out) || !aligned16(idx)) return cudaErrorInvalidValue;
+    const uint32_t n4 = n / 4;
+    k_gather_by_index4<<<grid_for(n4 ? n4 : 1), 256, 0, s>>>((uint4*)out, vals, (const uint4*)idx, n4, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pairs_pack(uint64_t* comp, const uint32_t* keys, uint32_t n, int desc, cudaStream_t s)
 {

@@ -170,6 +170,29 @@ def test_pairs_small(ascending, cap):
         assert np.array_equal(to_host(tk), wk) and np.array_equal(to_host(tv), wv), n
 
 
+@pytest.mark.parametrize("ascending", [True, False])
+def test_pairs_alignments_and_variants(ascending):
+    # The optimized plan builds the composites in its first tile launch and
+    # splits them in its last (vector accesses when keys and values are 8-byte
+    # aligned, element accesses otherwise; one launch does both up to 8192
+    # pairs); the basic and semi variants use separate pack, gather and split
+    # kernels.  Keys equal to 0xFFFFFFFF must still sort before the padding.
+    for n in [5, 8191, 8192, 8193, 16385, (1 << 20) + 1]:
+        keys = (workloads.uniform_u32(n, seed=n + 3) >> np.uint32(24)).astype(np.uint32)
+        keys[::7] = 0xFFFFFFFF
+        vals = workloads.uniform_u32(n, seed=n + 9)
+        wk, wv = oracle.merge_sort_pairs(keys, vals, ascending)
+        for kf, vf, variant in ((0, 0, 0), (1, 1, 0), (2, 0, 0), (0, 3, 0), (0, 0, 2), (1, 2, 1)):
+            if variant == 1 and n > (1 << 14):
+                continue
+            bt.set_options(variant=variant)
+            tk, tv = to_dev(keys, kf), to_dev(vals, vf)
+            bt.sort_pairs_(tk, tv, ascending)
+            torch.cuda.synchronize()
+            assert np.array_equal(to_host(tk), wk) and np.array_equal(to_host(tv), wv), (n, kf, vf, variant)
+    bt.set_options(variant=0)
+
+
 def test_pairs_n26_ties_by_index():
     # 2^26 pairs: keys uniform over [0, 2^20), values = original index
     keys, vals = workloads.pair_keys_u32(1 << 26, seed=workloads.SEEDS["pairs_n26"])
