@@ -361,20 +361,88 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline():
-    """Oracle network on one host core, ~10-20 s of work: 2^22 keys, repeated."""
-    import oracle
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
 
-    n = 1 << 22
-    keys = workloads.uniform_u32(n, seed=workloads.SEEDS["n28_uniform"])
-    reps, total = 0, 0.0
-    while total < 10.0 and reps < 8:
+
+def _timed(fn, keys, budget_s, max_reps=8):
+    """Runs fn(keys) until about budget_s seconds are spent; returns (out, seconds per call, calls)."""
+    reps, total, out = 0, 0.0, None
+    while (total < budget_s and reps < max_reps) or reps == 0:
         t0 = time.perf_counter()
-        oracle.bitonic_sort(keys)
+        out = fn(keys)
         total += time.perf_counter() - t0
         reps += 1
-    return {"value": n * reps / total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} x 2^22 uniform uint32 keys, Section 3.1 network in plain C"}
+    return out, total / reps, reps
+
+
+def cpu_baseline(gpu_gkeys_s=None):
+    """CPU sorts on the machine's host cores, each on a bounded sample of the
+    workload (uniform uint32 keys from the same generator), every output
+    checked against another CPU sort of the same input:
+      oracle_network_1core  the oracle's Section 3.1 network, plain C (the
+                            analogue of Table 1's CPU BitonicSort column);
+      quicksort_1core       the oracle's median-of-three Hoare quicksort (the
+                            CPU QuickSort column behind Section 5's speedups);
+      std_sort_1core        std::sort;
+      std_sort_all_cores    one std::sort per core, then parallel merges.
+    The line's value is the oracle network's rate."""
+    import oracle
+
+    nproc = os.cpu_count() or 1
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = nproc
+    full = workloads.uniform_u32(1 << 28, seed=workloads.SEEDS["n28_uniform"])
+    legs = {}
+    # oracle network on 2^22 keys (~10 s); quicksort of the same keys must agree
+    s22 = full[: 1 << 22].copy()
+    net, sec, reps = _timed(oracle.bitonic_sort, s22, 10.0)
+    net = net[0]
+    legs["oracle_network_1core"] = {"gkeys_s": s22.size / sec / 1e9, "n": s22.size, "calls": reps, "cores": 1}
+    q22 = oracle.quicksort(s22)
+    agree = bool(np.array_equal(net, q22))
+    # quicksort and std::sort on 2^25 keys, one core each; they must agree
+    s25 = full[: 1 << 25].copy()
+    q25, sec, reps = _timed(oracle.quicksort, s25, 4.0, 3)
+    legs["quicksort_1core"] = {"gkeys_s": s25.size / sec / 1e9, "n": s25.size, "calls": reps, "cores": 1}
+    st25, sec, reps = _timed(oracle.std_sort, s25, 4.0, 3)
+    legs["std_sort_1core"] = {"gkeys_s": s25.size / sec / 1e9, "n": s25.size, "calls": reps, "cores": 1}
+    agree &= bool(np.array_equal(q25, st25))
+    # every core on the full 2^28 array; its 2^25 prefix sort must agree too
+    p28, sec, reps = _timed(lambda a: oracle.parallel_sort(a, usable), full, 3.0, 3)
+    legs["std_sort_all_cores"] = {"gkeys_s": full.size / sec / 1e9, "n": full.size, "calls": reps, "cores": usable}
+    agree &= bool(np.array_equal(oracle.parallel_sort(s25, usable), q25))
+    agree &= bool(np.all(p28[1:] >= p28[:-1])) and int(p28.astype(np.uint64).sum()) == int(full.astype(np.uint64).sum())
+    out = {"value": legs["oracle_network_1core"]["gkeys_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{legs['oracle_network_1core']['calls']} x 2^22 uniform uint32 keys, Section 3.1 network in "
+                     "plain C; the other legs: quicksort and std::sort on 2^25 keys (one core), std::sort per "
+                     "core plus parallel merges on the full 2^28",
+           "cpu_model": cpu_model(), "nproc": nproc, "usable_cores": usable, "legs": legs,
+           "outputs_agree": agree}
+    if gpu_gkeys_s:
+        out["gpu_vs_quicksort_1core"] = gpu_gkeys_s / legs["quicksort_1core"]["gkeys_s"]
+        out["gpu_vs_std_sort_all_cores"] = gpu_gkeys_s / legs["std_sort_all_cores"]["gkeys_s"]
+        out["paper_gpu_vs_quicksort"] = ("about 20x, up to 30x (Kepler K10 against one Xeon E5-2620 core, "
+                                         "Section 5 / Table 1; context only)")
+    return out
 
 
 def main():
@@ -547,7 +615,7 @@ def main():
     if not args.no_serving and rank == 0:
         line["serving"] = serving_leg(bt, args.serving_requests)
     if not args.no_cpu_baseline and rank == 0:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(value)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -17,6 +17,8 @@ Functions and the passages they follow:
                         float64 keys (floats: IEEE 754-2008 totalOrder)
   merge_sort[_pairs]    independent stable top-down merge sort
   quicksort             Section 5 / Table 1 CPU comparison (median-of-three)
+  std_sort, parallel_sort  std::sort on one core / every core (cpu_baselines.cpp),
+                        the benchmark's modern CPU references
   zero_one_failures     0-1 principle over all 2^m zero-one inputs
   segmented_sort[_pairs] per-segment network, ascending
   is_sorted, same_multiset  checkers
@@ -181,6 +183,37 @@ def quicksort(keys, lib=None):
     lib = lib or load()
     a = _u32(keys)
     lib.oracle_quicksort_u32(_ptr(a), a.size)
+    return a
+
+
+_CPU_LIB = None
+
+
+def _cpu_lib() -> ctypes.CDLL:
+    """The benchmark's CPU comparison sorts (cpu_baselines.cpp)."""
+    global _CPU_LIB
+    if _CPU_LIB is None:
+        lib = ctypes.CDLL(_build.build_cpu())
+        lib.cpu_std_sort_u32.argtypes = [_P32, ctypes.c_uint64]
+        lib.cpu_std_sort_u32.restype = None
+        lib.cpu_parallel_sort_u32.argtypes = [_P32, ctypes.c_uint64, ctypes.c_int]
+        lib.cpu_parallel_sort_u32.restype = ctypes.c_int
+        _CPU_LIB = lib
+    return _CPU_LIB
+
+
+def std_sort(keys):
+    """std::sort on one core (a modern CPU reference beside Section 5's quicksort)."""
+    a = _u32(keys)
+    _cpu_lib().cpu_std_sort_u32(_ptr(a), a.size)
+    return a
+
+
+def parallel_sort(keys, threads: int):
+    """std::sort of one chunk per thread, then parallel pairwise merges."""
+    a = _u32(keys)
+    if _cpu_lib().cpu_parallel_sort_u32(_ptr(a), a.size, int(threads)) != 0:
+        raise MemoryError("parallel_sort: no scratch buffer")
     return a
 
 

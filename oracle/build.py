@@ -33,5 +33,27 @@ def build(force: bool = False, mutant: int = 0, out_dir: str | None = None) -> s
     return out
 
 
+CPU_SRC = os.path.join(HERE, "cpu_baselines.cpp")
+
+
+def cpu_lib_path(out_dir: str | None = None) -> str:
+    return os.path.join(out_dir or OUT_DIR, "libcpu_baselines.so")
+
+
+def build_cpu(force: bool = False, out_dir: str | None = None) -> str:
+    """The benchmark's CPU comparison sorts (std::sort on one core and on
+    every core), built with g++."""
+    out = cpu_lib_path(out_dir)
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(CPU_SRC):
+        return out
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-pthread", "-Wall", "-Wextra", CPU_SRC, "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))
+    print(build_cpu(force="--force" in sys.argv))

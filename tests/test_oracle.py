@@ -295,3 +295,17 @@ def test_typed_network_equals_library_sort(name, n):
 def test_typed_rejects_other_types():
     with pytest.raises(TypeError):
         oracle.bitonic_sort_typed(np.arange(4, dtype=np.int16))
+
+
+def test_cpu_comparison_sorts():
+    # The benchmark's CPU references (std::sort on one core; one std::sort per
+    # thread, then parallel merges) and the Section 5 quicksort agree with
+    # numpy's sort on seeded inputs, ragged sizes and thread counts included.
+    for n in (0, 1, 2, 3, 17, 1000, 65537, (1 << 20) + 3):
+        keys = workloads.uniform_u32(n, seed=n + 21)
+        keys[::5] = keys[0] if n else keys[::5]
+        want = np.sort(keys)
+        assert np.array_equal(oracle.std_sort(keys), want)
+        assert np.array_equal(oracle.quicksort(keys), want)
+        for threads in (1, 2, 3, 7, 16):
+            assert np.array_equal(oracle.parallel_sort(keys, threads), want), (n, threads)
