@@ -141,10 +141,13 @@ bitonic_status bitonic_sort_u32_host_batch(const uint32_t *const *in, uint32_t *
 /*
  * Sorts key/value pairs in place.  Keys compare first; equal keys keep their
  * original index order (ascending index in both directions), so the result is
- * unique.  vals[i] travels with keys[i].  Uses a workspace of 8 * N bytes
- * (one 64-bit composite (key', index) per element, key' = key or ~key) plus
- * 4 * n bytes for the value gather.  The network is Section 3.1's, run on the
- * composites.
+ * unique.  vals[i] travels with keys[i].  The network is Section 3.1's, run
+ * on 64-bit composites (key' << 32) | index, key' = key or ~key, held in a
+ * per-stream workspace of about 12 * n bytes: the first tile launch builds
+ * the composites while it loads the keys, the last writes the keys back and
+ * the original indices to the workspace, a gather kernel reads each value by
+ * its index into the workspace and a device copy puts the values back.  (The
+ * basic and semi variants use separate pack, gather and split kernels.)
  */
 bitonic_status bitonic_sort_pairs_u32(uint32_t *keys, uint32_t *vals, size_t n, int ascending,
                                       bitonic_stream_t stream);
@@ -156,16 +159,31 @@ bitonic_status bitonic_sort_pairs_u32(uint32_t *keys, uint32_t *vals, size_t n, 
  * segments are allowed.  Offsets are device-resident and are not validated
  * unless the environment variable BITONIC_DEBUG_CHECKS=1 is set, in which
  * case a violation is reported as BITONIC_ERR_INVALID by
- * bitonic_last_device_error().  Segments longer than the on-chip tile are
- * sorted with additional merge passes; to plan those passes the call reads a
- * 64-entry size histogram back to the host (one stream synchronisation) when
- * at least one segment exceeds the tile.
+ * bitonic_last_device_error().  The segments are binned by size on the
+ * device and nothing is read back to the host, so the call is one
+ * asynchronous launch sequence (it can be captured in a CUDA graph once a
+ * call of the same batch size has sized the stream's workspace).  Segments
+ * of up to 16384 keys are packed into shared-memory tiles, many per tile;
+ * each longer segment runs the launch plan of a sort of 2^k keys
+ * (k = ceil(log2 of its length plus its offset from a 16-byte boundary)):
+ * tile sort, multi-stride passes and tile merges.  All of a batch's long
+ * segments share one persistent launch whose CTAs take (pass, segment, tile)
+ * items in pass order; a tile waits, bounded, until its segment's previous
+ * pass is done, and a wait that gives up is reported as BITONIC_ERR_TIMEOUT
+ * by bitonic_last_device_error().  A segment longer than 2^31 - 3 keys is
+ * reported as BITONIC_ERR_INVALID and left unsorted.
  */
 bitonic_status bitonic_sort_segmented_u32(uint32_t *keys, const int32_t *offsets, int nseg,
                                           bitonic_stream_t stream);
 
 /* Segmented key/value sort: each segment sorted ascending by (key, index)
- * with its values, as bitonic_sort_pairs_u32 does for one array. */
+ * with its values, as bitonic_sort_pairs_u32 does for one array.  Segments
+ * of up to 8192 pairs are packed into tiles of 64-bit composites; a longer
+ * segment is sorted by one CTA running the network on composites in global
+ * memory.  When a segment may exceed 8192 pairs the call reads three ints
+ * back (the offsets' span and the longest segment, one stream
+ * synchronisation) to size the composite workspace, so it cannot be
+ * captured; bitonic_sort_segmented_pairs_u32_bounded avoids the read-back. */
 bitonic_status bitonic_sort_segmented_pairs_u32(uint32_t *keys, uint32_t *vals,
                                                 const int32_t *offsets, int nseg,
                                                 bitonic_stream_t stream);

@@ -29,6 +29,9 @@ constexpr int kDevBadOffsets = 1;
 constexpr int kDevTimeout = 2;
 
 constexpr size_t kMaxGraphs = 64;
+// Bound of each wait of the long-segment sort for a segment's previous pass
+// (polls about 128 ns apart: about half a second).
+constexpr uint32_t kLongWaitSpins = 1u << 22;
 constexpr uint64_t kMaxKeys = uint64_t(1) << 31;
 // Host-buffer sorts upload, tile-sort, final-pass and download in this many
 // chunks, so that copies overlap the passes that need only their own tiles.
@@ -111,6 +114,11 @@ struct DeviceState {
     int tile_blocks[kNumTileCfgs] = {};  // resident tile CTAs per SM, per configuration
     int* status = nullptr;               // device status word shared by every stream
     TileParamsBig* seg_descs[2] = {nullptr, nullptr};  // packed segment tiles by class: keys, pairs
+    // Segments longer than one tile (keys): the launch plans of sorts of
+    // 2^k keys, k = 15..31, built at the first segmented call.
+    bool long_ready = false;
+    LongPlans long_plans = {};
+    TileParamsBig* long_descs = nullptr;
     std::map<cudaStream_t, StreamWs> ws;
     std::map<PlanKey, std::unique_ptr<PlanEntry>> plans;
     std::map<GraphKey, GraphEntry> graphs;
@@ -168,6 +176,39 @@ bitonic_status device_state(DeviceState** out)
         ds.inited = true;
     }
     *out = &ds;
+    return BITONIC_OK;
+}
+
+// Descriptors of the plain sorts of 2^k keys, k = m+1..31 (default options,
+// 16K-key tiles), for the long segments of a segmented batch.
+bitonic_status ensure_long_plans(DeviceState& ds)
+{
+    if (ds.long_ready) return BITONIC_OK;
+    LongPlans lp = {};
+    lp.tile_log = 14;
+    std::vector<TileParamsBig> descs;
+    const Options o;
+    for (int k = lp.tile_log + 1; k <= 31; ++k) {
+        const Plan pl = make_plan(uint64_t(1) << k, 4, o);
+        if (!pl.ok || pl.cfg != 0 || (int)pl.launches.size() > kLongMaxPasses) {
+            t_last_error = "long-segment plans";
+            return BITONIC_ERR_UNSUPPORTED;
+        }
+        lp.npass[k] = (int)pl.launches.size();
+        lp.desc0[k] = (int)descs.size();
+        for (const Launch& L : pl.launches) {
+            if (L.desc < 0 || L.grid != (1u << (k - lp.tile_log))) {
+                t_last_error = "long-segment plans";
+                return BITONIC_ERR_UNSUPPORTED;
+            }
+            descs.push_back(pl.descs[L.desc]);
+        }
+    }
+    const size_t bytes = descs.size() * sizeof(TileParamsBig);
+    BT_CK(cudaMalloc(&ds.long_descs, bytes));
+    BT_CK(cudaMemcpy(ds.long_descs, descs.data(), bytes, cudaMemcpyHostToDevice));
+    ds.long_plans = lp;
+    ds.long_ready = true;
     return BITONIC_OK;
 }
 
@@ -787,8 +828,9 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
     DeviceState* ds;
     if ((st = device_state(&ds))) return st;
     StreamWs* w;
-    const size_t seg_need = seg_tiles_ws_bytes(nseg);
+    const size_t seg_need = vals ? seg_tiles_ws_bytes(nseg) : seg_long_ws_bytes(nseg);
     if ((st = stream_ws(*ds, s, 0, &w, seg_need))) return st;
+    if (!vals && (st = ensure_long_plans(*ds))) return st;
     // persistent packed-tile CTAs: as many as are resident
     const int tile_grid = (vals ? kSegTileBlocksPairs : kSegTileBlocksKeys) * ds->num_sms;
     const int large_grid = 4 * ds->num_sms;
@@ -798,7 +840,9 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
         return run_graphed(*ds, key, s, [&](cudaStream_t cs) -> bitonic_status {
             BT_CK(seg_tiles_launch(keys, nullptr, offsets, nseg, ws, ds->seg_descs[0], tile_grid, ds->status,
                                    debug_checks(), cs));
-            BT_CK(seg_launch_large(keys, nullptr, offsets, ws, nullptr, 0, large_grid, cs));
+            // segments longer than one tile: their own multi-pass plans, one persistent launch
+            BT_CK(seg_long_launch(keys, offsets, nseg, ws, ds->long_plans, ds->long_descs,
+                                  kSegTileBlocksKeys * ds->num_sms, ds->status, kLongWaitSpins, cs));
             return BITONIC_OK;
         });
     }

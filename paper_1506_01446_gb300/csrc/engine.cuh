@@ -177,6 +177,27 @@ __device__ __forceinline__ uint32_t io_thread_global(const IoDesc& io, uint32_t 
     return g;
 }
 
+// 16-byte global load; CG: cached in L2 only (ld.global.cg), for data that
+// other CTAs of the same launch wrote (the L1 of this SM may hold an older
+// copy of the line).
+template <bool CG, typename V>
+__device__ __forceinline__ V load_vec(const V* p)
+{
+    if constexpr (CG)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
+template <bool CG, typename K>
+__device__ __forceinline__ K load_key(const K* p)
+{
+    if constexpr (CG)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
 template <typename K>
 __device__ __forceinline__ void vec_to_regs(const typename KeyTraits<K>::Vec& w, K* r);
 
@@ -250,6 +271,7 @@ struct Tile {
 
     // Global load in the load round's layout.  base points at virtual
     // position 0; positions [lo, hi) hold real keys, others are pads.
+    template <bool CG = false>
     __device__ __forceinline__ void load_global(const K* __restrict__ base, uint32_t lo, uint32_t hi,
                                                 const IoDesc& io, uint32_t g0, uint32_t x, KeyMap<K> m)
     {
@@ -262,14 +284,14 @@ struct Tile {
             const uint32_t pos = gt ^ reg_local_index<NREG>(gr, v);
             K* dst = r + v * VEC;
             if (pos >= lo && pos + VEC <= hi) {
-                vec_to_regs<K>(*reinterpret_cast<const Vec*>(base + pos), dst);
+                vec_to_regs<K>(load_vec<CG>(reinterpret_cast<const Vec*>(base + pos)), dst);
 #pragma unroll
                 for (int c = 0; c < VEC; ++c) dst[c] = m(dst[c]);
             } else {
 #pragma unroll
                 for (int c = 0; c < VEC; ++c) {
                     const uint32_t p = pos + c;
-                    dst[c] = p < lo ? kFrontPad : (p >= hi ? kTailPad : m(base[p]));
+                    dst[c] = p < lo ? kFrontPad : (p >= hi ? kTailPad : m(load_key<CG>(base + p)));
                 }
             }
         }
@@ -314,6 +336,7 @@ struct Tile {
     }
 
     // Global load / store for tiles that lie wholly inside [lo, hi).
+    template <bool CG = false>
     __device__ __forceinline__ void load_global_interior(const K* __restrict__ base, const IoDesc& io, uint32_t g0,
                                                          uint32_t x, KeyMap<K> m)
     {
@@ -323,7 +346,8 @@ struct Tile {
         for (int j = 0; j < NREG; ++j) gr[j] = io.reg_glob[j];
 #pragma unroll
         for (int v = 0; v < NV; ++v)
-            vec_to_regs<K>(*reinterpret_cast<const Vec*>(base + (gt ^ reg_local_index<NREG>(gr, v))), r + v * VEC);
+            vec_to_regs<K>(load_vec<CG>(reinterpret_cast<const Vec*>(base + (gt ^ reg_local_index<NREG>(gr, v)))),
+                           r + v * VEC);
         apply_map(m);
     }
 

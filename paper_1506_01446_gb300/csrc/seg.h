@@ -31,6 +31,40 @@ struct SegPlan {
     int pad_;
 };
 
+// Segments longer than one tile (keys only): each runs the full launch plan
+// of a sort of N = 2^k keys (its tile sort, multi-stride and merge passes),
+// k = ceil(log2(front + length)), front = the segment's offset from a 16-byte
+// boundary.  plans holds, per k, the number of launches and the index of the
+// first launch's descriptor in the device descriptor array.
+constexpr int kLongMaxPasses = 48;
+struct LongPlans {
+    int npass[kSegClasses + 1];
+    int desc0[kSegClasses + 1];
+    int tile_log;  // m: log2 keys per tile of the plans
+};
+
+// Device-side schedule of one batch's long segments (built per call).
+struct LongSched {
+    int count[kSegClasses + 1];        // long segments per k
+    int class_start[kSegClasses + 1];  // first slot of class k (classes by k descending)
+    int cursor[kSegClasses + 1];
+    int pass_start[kLongMaxPasses + 1];  // first work item of each pass
+    int total_items;
+    int work;                          // persistent CTAs' work counter
+    int pad_[2];
+};
+
+// Workspace of the long-segment sort after the packed-tile one (16-byte aligned).
+size_t seg_long_ws_offset(int nseg);
+size_t seg_long_ws_bytes(int nseg);
+cudaError_t seg_long_init_attributes();
+// Sorts the batch's long segments (the packed-tile launch's large class,
+// listed in ws) with one persistent launch; max_spins bounds each wait for a
+// segment's previous pass.
+cudaError_t seg_long_launch(uint32_t* keys, const int32_t* offs, int nseg, void* ws, const LongPlans& plans,
+                            const TileParamsBig* descs, int grid, int* status, uint32_t max_spins,
+                            cudaStream_t s);
+
 cudaError_t seg_init_attributes();
 cudaError_t seg_tiles_init_attributes();
 size_t seg_tiles_ws_bytes(int nseg);

@@ -1,8 +1,9 @@
-// Segmented sort: segments longer than one tile, and the batch statistics
-// used to size the pair workspace.  Each long segment is sorted by one CTA
-// running the network of Section 3.1 (mirror form) on global memory with
-// block barriers between steps; persistent CTAs pull segments from an
-// atomic counter.
+// Segmented sort of pairs: segments longer than one tile, and the batch
+// statistics used to size the pair workspace.  Each long pair segment is
+// sorted by one CTA running the network of Section 3.1 (mirror form) on
+// global memory with block barriers between steps; persistent CTAs pull
+// segments from an atomic counter.  (Long keys-only segments run their
+// multi-pass plans instead: seg_long.cu.)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -116,7 +117,12 @@ __global__ void k_seg_complement(uint32_t* __restrict__ keys, const int32_t* __r
 
 }  // namespace
 
-cudaError_t seg_init_attributes() { return seg_tiles_init_attributes(); }
+cudaError_t seg_init_attributes()
+{
+    cudaError_t e = seg_tiles_init_attributes();
+    if (e == cudaSuccess) e = seg_long_init_attributes();
+    return e;
+}
 
 cudaError_t seg_launch_complement(uint32_t* keys, const int32_t* offs, int nseg, int grid, cudaStream_t s)
 {

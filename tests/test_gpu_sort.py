@@ -276,6 +276,48 @@ def test_segmented_descending(pairs):
     check_segmented_descending(keys, offs, pairs)
 
 
+@pytest.mark.parametrize("pad_front", [0, 1, 3])
+def test_segmented_long_segments(pad_front):
+    # Segments longer than one tile run the multi-pass plan of a 2^k-key sort
+    # (one persistent launch for all of them); among them 2^15, 2^17 and 2^20
+    # keys, lengths just past a tile and ragged ones, between small segments,
+    # with the keys array itself off a 16-byte boundary by pad_front keys.
+    lens = [5, 1 << 15, 0, 1 << 17, 100, 1 << 20, 16385, (1 << 15) + 3, 3, 40000, (1 << 18) - 1, 8192, 1,
+            (1 << 16) + 1, 2]
+    keys, offs = segments_case(lens, seed=31 + pad_front)
+    keys[::11] = keys[7]  # repeated keys
+    tk = to_dev(keys, pad_front)
+    to = torch.from_numpy(offs).cuda()
+    want = oracle.segmented_sort(keys, offs)
+    for _ in range(2):  # the second call reuses the workspace and the cached graph
+        tk.copy_(to_dev(keys, pad_front))
+        bt.sort_segmented_(tk, to)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(tk), want)
+    assert bt.last_device_error() == bt.OK
+    # descending: every segment reversed order, keys outside the segments untouched
+    tk = to_dev(keys, pad_front)
+    bt.sort_segmented_(tk, to, ascending=False)
+    wk = keys.copy()
+    for a, b in zip(offs[:-1], offs[1:]):
+        if b > a:
+            wk[a:b] = want[a:b][::-1]
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(tk), wk)
+
+
+def test_segmented_many_long_segments():
+    # 300 segments of 16385..70000 keys (a few passes each, many segments per
+    # size class) and one of 2^21: the work of every pass interleaves segments
+    rng = np.random.default_rng(4)
+    lens = rng.integers(16385, 70001, size=300).tolist() + [1 << 21]
+    keys, offs = segments_case(lens, seed=41)
+    tk = to_dev(keys)
+    bt.sort_segmented_(tk, torch.from_numpy(offs).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(tk), oracle.segmented_sort(keys, offs))
+
+
 def test_segmented_batched_workload():
     # 65,536 arrays, lengths log-uniform in [1, 8192]
     keys, offs = workloads.segmented_u32(65536, seed=workloads.SEEDS["segmented"])
