@@ -52,8 +52,8 @@ def parse():
                          "(so a profiled run repeats a timed run's configuration), else written")
     ap.add_argument("--no-pairs", action="store_true", help="skip the key/value leg")
     ap.add_argument("--no-key-types", action="store_true", help="skip the int32/float32/64-bit key leg")
-    ap.add_argument("--ablation", action="store_true",
-                    help="also time the paper's three GPU variants (Basic / Semi / Optimized) over its sizes")
+    ap.add_argument("--no-ablation", action="store_true",
+                    help="skip the paper's three GPU variants (Basic / Semi / Optimized) over its sizes")
     return ap.parse_args()
 
 
@@ -113,25 +113,55 @@ def segmented_leg(bt, torch, steps):
     lens = np.diff(offs_np).tolist()
     ptrs = (base + 4 * offs_np[:-1].astype(np.int64)).tolist()
     sh = stream.cuda_stream
-    for p, n in zip(ptrs[:256], lens[:256]):
-        lib.bitonic_sort_u32(p, n, 1, sh)
+    f = lib.bitonic_sort_u32
+    # every size class once outside any capture (plans, device state)
+    for n_ in sorted(set(lens)):
+        i_ = lens.index(n_)
+        f(ptrs[i_], n_, 1, sh)
     buf.copy_(src)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    f = lib.bitonic_sort_u32
-    for p, n in zip(ptrs, lens):
-        f(p, n, 1, sh)
+    for p, n_ in zip(ptrs, lens):
+        f(p, n_, 1, sh)
     b.record(stream)
     torch.cuda.synchronize()
-    per_array_ms = a.elapsed_time(b)
+    host_loop_ms = a.elapsed_time(b)
+    # the same 65,536 calls captured into one CUDA graph (the library enqueues
+    # straight into the caller's capture), replayed: the device-side cost of
+    # the per-array form without the host's per-call dispatch
+    cap = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=cap, capture_error_mode="thread_local"):
+        hc = cap.cuda_stream
+        for p, n_ in zip(ptrs, lens):
+            f(p, n_, 1, hc)
+    graph_times = []
+    for r in range(3):
+        buf.copy_(src)
+        torch.cuda.synchronize()
+        # replay() launches the graph on the current stream: time it there
+        rs = torch.cuda.current_stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(rs)
+        g.replay()
+        b.record(rs)
+        torch.cuda.synchronize()
+        graph_times.append(a.elapsed_time(b))
+    per_array_ms = statistics.median(graph_times)
     bt.set_options(**saved)
     out = buf.cpu().numpy().view(np.uint32)
     ok = all(np.all(np.diff(out[offs_np[i]:offs_np[i + 1]].astype(np.int64)) >= 0) for i in range(0, 65536, 97))
+    del g
     nkeys = int(offs_np[-1] - offs_np[0])
     return {"arrays": 65536, "keys": nkeys, "batched_ms": batched_ms, "batched_gkeys_s": nkeys / batched_ms / 1e6,
-            "per_array_ms": per_array_ms, "speedup": per_array_ms / batched_ms, "sampled_sorted": bool(ok),
-            "note": "per-array form = 65,536 bitonic_sort_u32 calls (plain launches) on one stream"}
+            "per_array_ms": per_array_ms, "speedup": per_array_ms / batched_ms,
+            "per_array_host_loop_ms": host_loop_ms, "speedup_vs_host_loop": host_loop_ms / batched_ms,
+            "sampled_sorted": bool(ok),
+            "note": "per-array form = 65,536 bitonic_sort_u32 calls on one stream, captured into one CUDA graph "
+                    "and replayed (median of 3); per_array_host_loop_ms = the same calls issued from a Python "
+                    "loop with plain launches"}
 
 
 def pairs_leg(bt, torch, steps):
@@ -230,19 +260,30 @@ def ablation_leg(bt, torch):
 
 
 def serving_leg(bt, requests):
-    """Poisson stream at 2,000 req/s, sizes log-uniform in [2^10, 2^22] keys,
-    30% with values, 16 GiB device budget, continuous batching."""
+    """Two offered loads, each a Poisson stream of `requests` requests, 30%
+    with values, 16 GiB device budget, continuous batching:
+      stated:  2,000 req/s, sizes log-uniform in [2^10, 2^22] keys (the
+               workload the latency target is quoted at);
+      batched_20k / batched_50k: 20,000 and 50,000 req/s, sizes log-uniform
+               in [2^10, 2^14] keys, where requests overlap and the loop
+               packs many into each launch."""
     from paper_1506_01446_gb300.serving import SortServer
-    arr, sizes, hv = workloads.serving_requests(requests, seed=workloads.SEEDS["serving"])
     pool = workloads.uniform_u32(1 << 26, seed=7)
     pool_v = np.arange(1 << 26, dtype=np.uint32)
     srv = SortServer(pool, pool_v, budget_bytes=16 << 30, streams=4)
-    srv.warmup(int(sizes.max()))                         # workspaces and plans before the clock starts
-    warm = min(200, requests)
-    srv.run(arr[:warm], sizes[:warm], hv[:warm])
-    stats = srv.run(arr, sizes, hv)
-    stats["rate_req_s"] = 2000.0
-    return stats
+    out = {}
+    for name, rate, hi_log2 in (("stated", 2000.0, 22), ("batched_20k", 20000.0, 14), ("batched_50k", 50000.0, 14)):
+        arr, sizes, hv = workloads.serving_requests(requests, seed=workloads.SEEDS["serving"], rate=rate,
+                                                    hi_log2=hi_log2)
+        srv.warmup(int(sizes.max()))                     # workspaces and plans before the clock starts
+        warm = min(200, requests)
+        srv.run(arr[:warm], sizes[:warm], hv[:warm])
+        stats = srv.run(arr, sizes, hv)
+        stats["rate_req_s"] = rate
+        stats["sizes"] = f"log-uniform [2^10, 2^{hi_log2}] keys, 30% with values"
+        out[name] = stats
+    # the stated point's numbers stay at the top level
+    return {**out["stated"], "points": out}
 
 
 def load_peaks():
@@ -578,6 +619,18 @@ def main():
         # download the last pass.
         host_in = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
         host_out = [torch.empty_like(host_in).pin_memory() for _ in range(2)]
+        # the host link alone, just before: one 1 GiB copy each way from and to
+        # page-locked memory (best of 3), so that a slow e2e step can be told
+        # apart from a slow link
+        link = {"h2d_gbs": 0.0, "d2h_gbs": 0.0}
+        for _ in range(3):
+            for name, dst, src_ in (("h2d_gbs", buf, host_in), ("d2h_gbs", host_out[0], buf)):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                dst.copy_(src_, non_blocking=True)
+                b.record(stream)
+                torch.cuda.synchronize()
+                link[name] = max(link[name], 4 * n / (a.elapsed_time(b) / 1e3) / 1e9)
         bt.sort_host_batch([host_in] * 2, host_out)  # warm-up: buffers, streams, plan
         torch.cuda.synchronize()
         # three timed batch calls, the median reported: the host link of a
@@ -601,14 +654,16 @@ def main():
                        "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms,
                        "runs_ms_per_step": runs, "timing": "median of 3 batch calls of K steps",
                        "api": "bitonic_sort_u32_host_batch (one call for the K steps)",
-                       "single_call_ms": la.elapsed_time(lb), "single_call_api": "bitonic_sort_u32_host"}
+                       "single_call_ms": la.elapsed_time(lb), "single_call_api": "bitonic_sort_u32_host",
+                       "link_gbs": link,
+                       "link_floor_ms": 4 * n / (link["h2d_gbs"] * 1e9) * 1e3 + 4 * n / (link["d2h_gbs"] * 1e9) * 1e3}
         out = host_out[0].numpy().view(np.uint32)
         assert np.all(out[1:] >= out[:-1])
     if not args.no_pairs and rank == 0:
         line["pairs"] = pairs_leg(bt, torch, max(3, args.steps))
     if not args.no_key_types and rank == 0:
         line["key_types"] = key_types_leg(bt, torch, max(3, args.steps), hbm_gbs)
-    if args.ablation and rank == 0:
+    if not args.no_ablation and rank == 0:
         line["ablation"] = ablation_leg(bt, torch)
     if not args.no_segmented and rank == 0:
         line["segmented"] = segmented_leg(bt, torch, max(3, args.steps))

@@ -278,6 +278,31 @@ bitonic_status bitonic_set_options(const bitonic_options *opt);
 bitonic_status bitonic_get_options(bitonic_options *opt);
 
 /*
+ * Graph replay for the calls this host thread makes from now on: mode 1 =
+ * replay cached CUDA graphs, 0 = plain launches, -1 = follow the
+ * process-wide use_graph option (the default).  Other threads are not
+ * affected.  A caller whose buffers change on every call (a server with
+ * fresh buffers per request) turns graphs off for its own thread instead of
+ * for the whole process.  BITONIC_ERR_INVALID for any other mode.
+ */
+bitonic_status bitonic_set_thread_graphs(int mode);
+
+/*
+ * Testing aid for the device-side failure path (no paper counterpart).
+ * starve_copies != 0: from now on every CTA of the pipelined tile kernels
+ * (option pipeline = 1) arms its mbarrier for its first tile's bulk copies
+ * but issues none of them, and each mbarrier wait gives up after max_spins
+ * tries (max_spins >= 1); the kernel then writes BITONIC_ERR_TIMEOUT to the
+ * device status word and returns with no copy in flight, so
+ * bitonic_last_device_error() reports the timeout and the context stays
+ * usable.  starve_copies == 0 restores normal copies and the default bound
+ * (max_spins ignored).  Synchronises the device first; the setting applies to
+ * the current device.  BITONIC_ERR_INVALID if starve_copies != 0 and
+ * max_spins == 0.
+ */
+bitonic_status bitonic_debug_set_wait(int starve_copies, unsigned max_spins);
+
+/*
  * Tuned choice for one size class: sorts of N = 2^log2_n keys of key_bytes
  * bytes (4: bitonic_sort_u32, 8: the composites of bitonic_sort_pairs_u32)
  * use opt's tile_log2, keys_per_thread_log2, global_bits and pipeline

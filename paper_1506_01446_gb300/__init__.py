@@ -31,7 +31,8 @@ EXPORTS = (
     "bitonic_debug_desc_size", "bitonic_sort_pairs_u32_noalloc", "bitonic_sort_segmented_pairs_u32_bounded",
     "bitonic_set_class_options", "bitonic_sort_i32", "bitonic_sort_f32", "bitonic_sort_u64", "bitonic_sort_i64",
     "bitonic_sort_f64", "bitonic_sort_u32_host", "bitonic_sort_u32_host_batch",
-    "bitonic_sort_segmented_u32_dir", "bitonic_sort_segmented_pairs_u32_dir",
+    "bitonic_sort_segmented_u32_dir", "bitonic_sort_segmented_pairs_u32_dir", "bitonic_set_thread_graphs",
+    "bitonic_debug_set_wait",
 )
 
 # torch dtype name -> C entry point of the keys-only sorts (uint64 keys may be
@@ -95,6 +96,8 @@ def load() -> ctypes.CDLL:
     lib.bitonic_sort_pairs_u32_noalloc.argtypes = [vp, vp, sz, i32, vp]
     lib.bitonic_sort_segmented_pairs_u32_bounded.argtypes = [vp, vp, vp, i32, i32, vp]
     lib.bitonic_set_class_options.argtypes = [i32, i32, ctypes.POINTER(Options)]
+    lib.bitonic_set_thread_graphs.argtypes = [i32]
+    lib.bitonic_debug_set_wait.argtypes = [i32, ctypes.c_uint]
     for name in EXPORTS:
         f = getattr(lib, name)
         if f.restype is ctypes.c_int or f.restype is None:
@@ -282,6 +285,28 @@ def set_options(variant=None, tile_log2=None, global_bits=None, use_graph=None,
             cur[k] = int(v)
     _check(load().bitonic_set_options(ctypes.byref(Options(**cur))), "bitonic_set_options")
     return cur
+
+
+def debug_set_wait(starve_copies: bool, max_spins: int = 0):
+    """Testing aid: the pipelined kernels' copy-starving mode with a short
+    wait bound (their waits then time out), or normal operation."""
+    _check(load().bitonic_debug_set_wait(int(bool(starve_copies)), int(max_spins)), "bitonic_debug_set_wait")
+
+
+class thread_graphs:
+    """Context manager: graph replay on (True), off (False) or following the
+    process-wide option (None) for the library calls of this host thread."""
+
+    def __init__(self, enabled):
+        self.mode = -1 if enabled is None else int(bool(enabled))
+
+    def __enter__(self):
+        _check(load().bitonic_set_thread_graphs(self.mode), "bitonic_set_thread_graphs")
+        return self
+
+    def __exit__(self, *exc):
+        load().bitonic_set_thread_graphs(-1)
+        return False
 
 
 def set_class_options(key_bytes: int, log2_n: int, options: dict | None):

@@ -22,6 +22,9 @@ namespace bitonic {
 namespace {
 
 thread_local std::string t_last_error;
+// Graph replay for calls from this host thread: -1 = the process-wide
+// use_graph option, 0 = plain launches, 1 = replay cached graphs.
+thread_local int t_graph_mode = -1;
 
 // Device status word values.
 constexpr int kDevOk = 0;
@@ -445,7 +448,8 @@ bitonic_status run_graphed(DeviceState& ds, const GraphKey& key, cudaStream_t us
 {
     cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
     BT_CK(cudaStreamIsCapturing(user, &cst));
-    if (!g_opt.use_graph || cst != cudaStreamCaptureStatusNone) return enqueue(user);
+    const bool graphs = t_graph_mode < 0 ? g_opt.use_graph != 0 : t_graph_mode != 0;
+    if (!graphs || cst != cudaStreamCaptureStatusNone) return enqueue(user);
     auto it = ds.graphs.find(key);
     if (it == ds.graphs.end()) {
         BT_CK(cudaStreamBeginCapture(ds.capture, cudaStreamCaptureModeThreadLocal));
@@ -1086,6 +1090,27 @@ bitonic_status bitonic_set_options(const bitonic_options* opt)
     g_opt.min_row_log2 = (opt->min_row_log2 < 0 || opt->min_row_log2 > 12) ? 0 : opt->min_row_log2;
     g_opt.ctas_per_sm = (opt->ctas_per_sm == 2 || opt->ctas_per_sm == 3) ? opt->ctas_per_sm : 0;
     g_opt.round_sync = opt->round_sync ? 1 : 0;
+    return BITONIC_OK;
+}
+
+bitonic_status bitonic_debug_set_wait(int starve_copies, unsigned max_spins)
+{
+    if (starve_copies && max_spins == 0) return BITONIC_ERR_INVALID;
+    std::lock_guard<std::mutex> g(g_mu);
+    DeviceState* ds;
+    bitonic_status st = device_state(&ds);
+    if (st) return st;
+    BT_CK(cudaDeviceSynchronize());
+    // a short bound only together with the starving mode: then no copy is in
+    // flight when a wait gives up
+    BT_CK(set_pipe_wait(starve_copies ? max_spins : 0u, starve_copies ? 1 : 0));
+    return BITONIC_OK;
+}
+
+bitonic_status bitonic_set_thread_graphs(int mode)
+{
+    if (mode < -1 || mode > 1) return BITONIC_ERR_INVALID;
+    t_graph_mode = mode;
     return BITONIC_OK;
 }
 

@@ -73,6 +73,9 @@ cudaError_t launch_pipe(int mode, int cfg, void* base, uint32_t lo, uint32_t hi,
                         const TileParamsBig* dP, uint32_t ntiles, uint32_t grid, uint64_t xor_in,
                         uint64_t xor_out, int* status, cudaStream_t s);
 cudaError_t init_pipe_attributes(int* blocks_per_sm);
+// Bound of the pipelined kernels' mbarrier waits on the current device (0 =
+// the default), and their copy-starving test mode.
+cudaError_t set_pipe_wait(uint32_t max_spins, int starve);
 cudaError_t launch_step(int key_bytes, int desc, void* base, uint32_t lo, uint32_t hi, uint32_t N, int j,
                         int flip, cudaStream_t s);
 

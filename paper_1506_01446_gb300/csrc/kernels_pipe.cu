@@ -17,6 +17,13 @@ namespace bitonic {
 
 namespace {
 
+// Bound of each mbarrier wait (tries), and the copy-starving test mode: when
+// set, each CTA arms its barrier for its first tile's bulk copies but issues
+// none of them, so its first wait runs out with no copy in flight and the
+// kernel reports a timeout (bitonic_debug_set_wait).
+__device__ uint32_t g_pipe_wait_spins = kMaxWaitSpins;
+__device__ int g_pipe_starve = 0;
+
 // Shared memory: [landing tile][transpose tile][mbarrier][fill count][fill rows].
 template <typename K, int M>
 struct PipeSmem {
@@ -74,14 +81,17 @@ __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uin
     // the barrier's transaction count goes below zero until thread 0's
     // arrive.expect_tx adds the total, and the phase cannot complete before
     // that arrival.
+    const uint32_t max_spins = g_pipe_wait_spins;
+    const bool starve = g_pipe_starve != 0;
     auto issue_tma = [&](uint32_t t) {
         const uint32_t g0 = cta_base(P, t);
+        const bool skip = starve && t == blockIdx.x;  // test mode: the first tile's copies never start
         fence_proxy_async_smem();
         for (uint32_t r = x; r < nrows; r += kThreads) {
             const uint32_t g = g0 ^ row_global(P, c, r);
-            if (g >= lo && g + row_len <= hi)
-                tma_load_bulk(X + (size_t)r * row_len, base + g, row_len * (uint32_t)sizeof(K), bar);
-            else
+            if (g >= lo && g + row_len <= hi) {
+                if (!skip) tma_load_bulk(X + (size_t)r * row_len, base + g, row_len * (uint32_t)sizeof(K), bar);
+            } else
                 fill_rows[atomicAdd(fill_count, 1u)] = (uint16_t)r;
         }
         __syncthreads();
@@ -138,7 +148,7 @@ __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uin
     for (; tile < ntiles; tile += gridDim.x) {
         bool ok = true;
         if constexpr (ASYNC == 0) {
-            ok = mbar_wait_bounded(bar, parity);
+            ok = mbar_wait_bounded(bar, parity, max_spins);
             parity ^= 1u;
         } else {
             asm volatile("cp.async.wait_all;" ::: "memory");
@@ -147,7 +157,7 @@ __device__ __forceinline__ void pipe_pass(K* __restrict__ base, uint32_t lo, uin
         t.smem_read_linear(reinterpret_cast<const Vec*>(X), P.rounds[0], x, cm_in);
         if (__syncthreads_or(!ok)) {
             if (x == 0) atomicCAS(status, 0, kStatusTimeout);
-            if constexpr (ASYNC == 0) mbar_wait_bounded(bar, parity ^ 1u);  // one more bounded wait for copies
+            if constexpr (ASYNC == 0) mbar_wait_bounded(bar, parity ^ 1u, max_spins);  // one more bounded wait for copies
             return;
         }
         const uint32_t g0 = cta_base(P, tile);
@@ -234,6 +244,14 @@ cudaError_t launch_pipe(int mode, int cfg, void* base, uint32_t lo, uint32_t hi,
         default: return cudaErrorInvalidValue;
     }
 #undef BITONIC_PIPE_CASE
+}
+
+cudaError_t set_pipe_wait(uint32_t max_spins, int starve)
+{
+    if (max_spins == 0) max_spins = kMaxWaitSpins;
+    cudaError_t e = cudaMemcpyToSymbol(g_pipe_wait_spins, &max_spins, sizeof(max_spins));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_pipe_starve, &starve, sizeof(starve));
+    return e;
 }
 
 // Sets the shared-memory limit of every pipelined kernel on the current

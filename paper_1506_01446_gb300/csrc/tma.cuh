@@ -51,10 +51,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 }
 
 // Waits for phase `parity` of the barrier; false if it did not complete
-// within kMaxWaitSpins tries.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+// within max_spins tries.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t max_spins)
 {
-    for (uint32_t i = 0; i < kMaxWaitSpins; ++i)
+    for (uint32_t i = 0; i < max_spins; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

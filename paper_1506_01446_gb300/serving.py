@@ -26,7 +26,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import load, OK, status_string, set_options, get_options
+from . import load, OK, status_string, thread_graphs
 
 ALIGN = 16
 
@@ -239,15 +239,13 @@ class SortServer:
         up to max_keys, so no request pays for a cudaMalloc (which
         synchronises) or for host-side planning."""
         torch = self.torch
-        saved = get_options()
-        set_options(use_graph=0)
-        try:
+        with thread_graphs(False):
             n_max = min(max_keys, self.in_keys.numel())
             k = self.dev[:4 * n_max].view(torch.int32)
             v = self.dev[4 * n_max:8 * n_max].view(torch.int32)
             k.copy_(self.in_keys[:n_max])
             v.copy_(self.in_vals[:n_max])
-            nb = min(self.max_batch, max(1, n_max // max(self.small_keys, 1)))
+            nb = max(1, min(self.max_batch, n_max))  # the largest packed batch sizes the segmented workspace
             offs = torch.arange(0, nb + 1, dtype=torch.int32, device="cuda") * min(self.small_pairs, n_max // nb)
             for stream in self.streams:
                 sh = stream.cuda_stream
@@ -265,16 +263,12 @@ class SortServer:
                         if st != OK:
                             raise RuntimeError(status_string(st))
             torch.cuda.synchronize()
-        finally:
-            set_options(**saved)
 
     # -- the loop --------------------------------------------------------------
     def run(self, arrival_s, sizes, has_vals, keep_outputs: bool = False):
         """Serves the request stream; returns a statistics dict (and, with
         keep_outputs, the sorted keys / values of every request)."""
         torch = self.torch
-        saved = get_options()
-        set_options(use_graph=0)  # every launch has fresh buffers: no graph reuse
         self._rr = 0
         reqs = []
         for i, (a, n, hv) in enumerate(zip(arrival_s, sizes, has_vals)):
@@ -286,7 +280,9 @@ class SortServer:
         nxt, done, n_batches, n_large, batch_sizes = 0, 0, 0, 0, []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        try:
+        # every launch has fresh buffers, so no cached graph would be replayed:
+        # plain launches, for this thread's calls only
+        with thread_graphs(False):
             while done < N:
                 now = time.perf_counter() - t0
                 while nxt < N and reqs[nxt].arrival <= now:
@@ -364,8 +360,6 @@ class SortServer:
                     wait = reqs[nxt].arrival - (time.perf_counter() - t0)
                     if wait > 2e-4:
                         time.sleep(wait - 1e-4)
-        finally:
-            set_options(**saved)
         lat = np.array([r.done - r.arrival for r in reqs])
         keys_total = int(sum(r.n for r in reqs))
         span = max(r.done for r in reqs) - min(r.arrival for r in reqs)

@@ -85,3 +85,20 @@ def test_options_validation():
         assert bt.get_options()["variant"] == 2
     finally:
         bt.set_options(**saved)
+
+
+def test_thread_graph_mode_validation():
+    lib = bt.load()
+    for mode in (-1, 0, 1):
+        assert lib.bitonic_set_thread_graphs(mode) == bt.OK
+    for mode in (-2, 2, 7):
+        assert lib.bitonic_set_thread_graphs(mode) == bt.ERR_INVALID
+    with bt.thread_graphs(False):
+        pass
+    assert lib.bitonic_set_thread_graphs(-1) == bt.OK
+
+
+def test_debug_wait_argument_check_needs_no_gpu():
+    # a starving test mode needs a bound of at least one try (checked before
+    # any device work)
+    assert bt.load().bitonic_debug_set_wait(1, 0) == bt.ERR_INVALID

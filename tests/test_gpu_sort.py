@@ -173,10 +173,11 @@ def test_pairs_small(ascending, cap):
 @pytest.mark.parametrize("ascending", [True, False])
 def test_pairs_alignments_and_variants(ascending):
     # The optimized plan builds the composites in its first tile launch and
-    # splits them in its last (vector accesses when keys and values are 8-byte
+    # splits them in its last (vector accesses when the keys are 8-byte
     # aligned, element accesses otherwise; one launch does both up to 8192
-    # pairs); the basic and semi variants use separate pack, gather and split
-    # kernels.  Keys equal to 0xFFFFFFFF must still sort before the padding.
+    # pairs), then gathers the values by index; the basic and semi variants
+    # use separate pack, gather and split kernels.  Keys equal to 0xFFFFFFFF
+    # must still sort before the padding.
     for n in [5, 8191, 8192, 8193, 16385, (1 << 20) + 1]:
         keys = (workloads.uniform_u32(n, seed=n + 3) >> np.uint32(24)).astype(np.uint32)
         keys[::7] = 0xFFFFFFFF
@@ -191,6 +192,30 @@ def test_pairs_alignments_and_variants(ascending):
             torch.cuda.synchronize()
             assert np.array_equal(to_host(tk), wk) and np.array_equal(to_host(tv), wv), (n, kf, vf, variant)
     bt.set_options(variant=0)
+
+
+def test_bounded_wait_times_out_and_context_stays_usable():
+    # The pipelined kernels' mbarrier waits are bounded.  In the test mode
+    # each CTA arms its barrier for its first tile's bulk copies but issues
+    # none, so with a bound of 8 tries its wait runs out with no copy in
+    # flight: the kernel writes BITONIC_ERR_TIMEOUT to the device status word
+    # and returns.  A normal sort on the same context afterwards is exact.
+    keys = workloads.uniform_u32(1 << 20, seed=19)
+    bt.set_options(pipeline=1, use_graph=0)
+    try:
+        bt.debug_set_wait(True, 8)
+        t = to_dev(keys)
+        bt.sort_(t)
+        assert bt.last_device_error() == bt.ERR_TIMEOUT
+    finally:
+        bt.debug_set_wait(False)
+    assert bt.last_device_error() == bt.OK
+    for pipeline in (1, 0):
+        bt.set_options(pipeline=pipeline, use_graph=1)
+        t = to_dev(keys)
+        bt.sort_(t)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(t), oracle.merge_sort(keys)), pipeline
 
 
 def test_pairs_n26_ties_by_index():

@@ -73,3 +73,44 @@ def test_tiny_budget_still_serves_everything():
     assert all(o is not None for o in outs)
     for (k, v), (_, n, has_v) in zip(outs, reqs):
         assert k.size == n and np.all(k[1:] >= k[:-1])
+
+
+@pytest.mark.gpu
+def test_batched_stream_packs_many_requests_and_matches_oracle():
+    # A stream fast enough that requests overlap (200,000 req/s, sizes up to
+    # 2^14 keys): the loop packs many requests into each segmented launch,
+    # and every result is still exactly the oracle's and the same as the
+    # request sorted alone.
+    import paper_1506_01446_gb300 as bt
+    srv, stats, outs, reqs, pool, pool_v, torch = _serve(600, 7, 1 << 30, hi_log2=14, rate=200000.0)
+    assert stats["mean_batch"] > 4, stats
+    probe = type(srv).__new__(type(srv))
+    probe.rings, probe.ring_pos = srv.rings, {k: 0 for k in srv.rings}
+    for i, (kind, n, has_v) in enumerate(reqs):
+        src = type(srv)._src(probe, kind, n)
+        k_in, v_in = pool[src:src + n], pool_v[src:src + n]
+        got_k, got_v = outs[i]
+        if has_v:
+            wk, wv = oracle.merge_sort_pairs(k_in, v_in)
+            assert np.array_equal(got_k, wk) and np.array_equal(got_v, wv), i
+        else:
+            assert np.array_equal(got_k, oracle.merge_sort(k_in)), i
+        if i % 50 == 0:  # the same request alone
+            tk = torch.from_numpy(k_in.view(np.int32).copy()).cuda()
+            if has_v:
+                tv = torch.from_numpy(v_in.view(np.int32).copy()).cuda()
+                bt.sort_pairs_(tk, tv)
+                assert np.array_equal(tv.cpu().numpy().view(np.uint32), got_v)
+            else:
+                bt.sort_(tk)
+            assert np.array_equal(tk.cpu().numpy().view(np.uint32), got_k)
+
+
+@pytest.mark.gpu
+def test_server_leaves_other_threads_graph_mode_alone():
+    # The server turns graph replay off for its own thread only: the
+    # process-wide option is unchanged during and after a run.
+    import paper_1506_01446_gb300 as bt
+    before = bt.get_options()["use_graph"]
+    _serve(40, 11, 1 << 28, hi_log2=15)
+    assert bt.get_options()["use_graph"] == before
