@@ -354,10 +354,10 @@ size_t bitonic_debug_desc_size(void);
  * Key/value sort that allocates no device memory (the paper has no
  * counterpart; this is a deployment variant of bitonic_sort_pairs_u32).
  *
- * For callers that cannot let the library call cudaMalloc: work recorded
- * while a stream is being captured into a CUDA graph, applications whose own
- * memory manager owns the device memory, and latency-critical paths that
- * cannot afford cudaMalloc's implicit synchronisation.  Same arguments,
+ * For callers that cannot let the library call cudaMalloc: applications
+ * whose own memory manager owns all of the device memory and forbids
+ * allocations behind its back, and latency-critical paths that cannot afford
+ * cudaMalloc's implicit synchronisation with the device.  Same arguments,
  * ordering and result as bitonic_sort_pairs_u32, but the 64-bit composites
  * live in a fixed array of 2^20 entries (8 MiB) compiled into the library,
  * which every GPU that loads the library holds until the process exits.
@@ -365,9 +365,10 @@ size_t bitonic_debug_desc_size(void);
  *   - The first call on a device looks up the array's address and sets the
  *     kernels' shared-memory limit (no allocation); make that first call
  *     before any stream capture on the device.
- *   - All calls on a device share the one array: calls whose work overlaps
- *     on the GPU (different streams, or graphs replayed concurrently) race
- *     and give wrong results.  Order them on one stream.
+ *   - All calls on a device share the one array, which keeps the last
+ *     call's contents: calls whose work overlaps on the GPU (for instance on
+ *     different streams) race and give wrong results.  Order them on one
+ *     stream.
  *   - Launches go straight to `stream` (no cached graph), with the default
  *     tile configuration regardless of bitonic_set_options.
  */

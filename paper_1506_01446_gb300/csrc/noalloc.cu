@@ -2,12 +2,10 @@
 //
 // bitonic_sort_pairs_u32 keeps its 64-bit (key, index) composites in a
 // workspace it grows with cudaMalloc.  Some callers cannot let a library do
-// that: code running while a stream is being captured into a CUDA graph
-// (allocation is not a capturable operation), applications whose memory
-// manager owns all device memory and forbids allocations behind its back,
-// and latency-critical paths where cudaMalloc's implicit synchronisation is
-// not acceptable.  This entry point keeps the composites in a fixed array in
-// the library's own device image instead.
+// that: applications whose memory manager owns all device memory and forbids
+// allocations behind its back, and latency-critical paths where cudaMalloc's
+// implicit synchronisation is not acceptable.  This entry point keeps the
+// composites in a fixed array in the library's own device image instead.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
