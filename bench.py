@@ -83,10 +83,16 @@ def measured_traffic(n):
     return d["bytes_per_launch"] * n / d["n"]
 
 
-def segmented_leg(bt, torch, steps):
+def segmented_leg(bt, torch, steps, tune_cache=None):
     """65,536 uint32 arrays (lengths log-uniform in [1, 8192]) sorted by one
-    batched segmented call vs one bitonic_sort_u32 call per array."""
+    batched segmented call vs one bitonic_sort_u32 call per array.  With a
+    tune_cache path the packed-tile launch is autotuned for the batch first."""
     keys_np, offs_np = workloads.segmented_u32(65536, seed=workloads.SEEDS["segmented"])
+    tuned = None
+    if tune_cache:
+        from paper_1506_01446_gb300 import autotune
+        tuned = autotune.tune_segmented(keys_np, offs_np, reps=3, cache_path=tune_cache)
+        tuned = {k: v for k, v in tuned.items() if k != "tried"}
     src = torch.from_numpy(keys_np.view(np.int32)).cuda()
     buf = src.clone()
     offs = torch.from_numpy(offs_np).cuda()
@@ -158,7 +164,7 @@ def segmented_leg(bt, torch, steps):
     return {"arrays": 65536, "keys": nkeys, "batched_ms": batched_ms, "batched_gkeys_s": nkeys / batched_ms / 1e6,
             "per_array_ms": per_array_ms, "speedup": per_array_ms / batched_ms,
             "per_array_host_loop_ms": host_loop_ms, "speedup_vs_host_loop": host_loop_ms / batched_ms,
-            "sampled_sorted": bool(ok),
+            "sampled_sorted": bool(ok), "tuned": tuned,
             "note": "per-array form = 65,536 bitonic_sort_u32 calls on one stream, captured into one CUDA graph "
                     "and replayed (median of 3); per_array_host_loop_ms = the same calls issued from a Python "
                     "loop with plain launches"}
@@ -504,8 +510,9 @@ def main():
     hbm_gbs, peak_src = load_peaks()
     keys_np = workloads.uniform_u32(n, seed=replica_seed(rank))
     tuned = None
+    import tempfile
+    seg_cache = os.path.join(tempfile.gettempdir(), f"bitonic_tune_seg_{rank}.json")
     if not args.no_tune:
-        import tempfile
         from paper_1506_01446_gb300 import autotune
         cache = args.tune_cache or os.path.join(tempfile.gettempdir(), f"bitonic_tune_{rank}.json")
         choices = autotune.load(cache) if args.tune_cache else None
@@ -666,7 +673,7 @@ def main():
     if not args.no_ablation and rank == 0:
         line["ablation"] = ablation_leg(bt, torch)
     if not args.no_segmented and rank == 0:
-        line["segmented"] = segmented_leg(bt, torch, max(3, args.steps))
+        line["segmented"] = segmented_leg(bt, torch, max(3, args.steps), None if args.no_tune else seg_cache)
     if not args.no_serving and rank == 0:
         line["serving"] = serving_leg(bt, args.serving_requests)
     if not args.no_cpu_baseline and rank == 0:

@@ -278,6 +278,23 @@ bitonic_status bitonic_set_options(const bitonic_options *opt);
 bitonic_status bitonic_get_options(bitonic_options *opt);
 
 /*
+ * Tuned choice for the packed-tile launch of segmented sorts whose segment
+ * count has ceil(log2 nseg) == log2_nseg (pairs != 0: the pair sorts).
+ * Written by the autotuner (paper_1506_01446_gb300.autotune); opt == NULL
+ * removes the class's choice.  Zero fields keep the defaults.
+ */
+typedef struct {
+    int tile_log2;        /* keys: 14 = 16K-key tiles (256 threads x 64 keys, default) or
+                             13 = 8K-key tiles (256 x 32); pairs: 13 (8K composites) */
+    int class_floor_gap;  /* 1..10: a segment of L keys is padded to 2^max(ceil(log2 L),
+                             tile_log2 - gap) positions, so a tile holds at most 2^gap segments
+                             (default 10) */
+    int ctas_per_sm;      /* 1 or 2 persistent CTAs per SM (default 2) */
+} bitonic_seg_options;
+
+bitonic_status bitonic_set_segmented_options(int pairs, int log2_nseg, const bitonic_seg_options *opt);
+
+/*
  * Graph replay for the calls this host thread makes from now on: mode 1 =
  * replay cached CUDA graphs, 0 = plain launches, -1 = follow the
  * process-wide use_graph option (the default).  Other threads are not

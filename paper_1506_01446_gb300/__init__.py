@@ -32,7 +32,7 @@ EXPORTS = (
     "bitonic_set_class_options", "bitonic_sort_i32", "bitonic_sort_f32", "bitonic_sort_u64", "bitonic_sort_i64",
     "bitonic_sort_f64", "bitonic_sort_u32_host", "bitonic_sort_u32_host_batch",
     "bitonic_sort_segmented_u32_dir", "bitonic_sort_segmented_pairs_u32_dir", "bitonic_set_thread_graphs",
-    "bitonic_debug_set_wait",
+    "bitonic_debug_set_wait", "bitonic_set_segmented_options",
 )
 
 # torch dtype name -> C entry point of the keys-only sorts (uint64 keys may be
@@ -53,6 +53,10 @@ class Options(ctypes.Structure):
                 ("keys_per_thread_log2", ctypes.c_int), ("io_direct", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("min_row_log2", ctypes.c_int), ("l2_prefetch", ctypes.c_int),
                 ("pipeline", ctypes.c_int), ("round_sync", ctypes.c_int)]
+
+
+class SegOptions(ctypes.Structure):
+    _fields_ = [("tile_log2", ctypes.c_int), ("class_floor_gap", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
 
 
 _lib = None
@@ -98,6 +102,7 @@ def load() -> ctypes.CDLL:
     lib.bitonic_set_class_options.argtypes = [i32, i32, ctypes.POINTER(Options)]
     lib.bitonic_set_thread_graphs.argtypes = [i32]
     lib.bitonic_debug_set_wait.argtypes = [i32, ctypes.c_uint]
+    lib.bitonic_set_segmented_options.argtypes = [i32, i32, ctypes.POINTER(SegOptions)]
     for name in EXPORTS:
         f = getattr(lib, name)
         if f.restype is ctypes.c_int or f.restype is None:
@@ -307,6 +312,16 @@ class thread_graphs:
     def __exit__(self, *exc):
         load().bitonic_set_thread_graphs(-1)
         return False
+
+
+def set_segmented_options(pairs: bool, log2_nseg: int, options: dict | None):
+    """Installs (or with None removes) the packed-tile choice of segmented
+    sorts of 2^(log2_nseg - 1) < nseg <= 2^log2_nseg segments."""
+    ptr = None
+    if options is not None:
+        ptr = ctypes.byref(SegOptions(**{**{f: 0 for f, _ in SegOptions._fields_}, **options}))
+    _check(load().bitonic_set_segmented_options(int(bool(pairs)), int(log2_nseg), ptr),
+           "bitonic_set_segmented_options")
 
 
 def set_class_options(key_bytes: int, log2_n: int, options: dict | None):

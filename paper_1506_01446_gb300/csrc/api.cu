@@ -69,6 +69,29 @@ struct PlanEntry {
     TileParamsBig* d_descs = nullptr;  // device copies, used by launches too big to pass by value
 };
 
+// Packed-tile choices of a segmented batch, per (pairs, ceil(log2 nseg))
+// class, set by the autotuner: tile size, smallest size class (m - gap) and
+// resident CTAs per SM of the persistent grid.  Zero fields: defaults.
+struct SegOpt {
+    int tile_log2 = 0;  // keys: 14 (16K keys, 256 x 64) or 13 (8K, 256 x 32); pairs: 13
+    int floor_gap = 0;  // 1..10 (default 10: up to 1024 segments per tile)
+    int ctas_per_sm = 0;  // 1 or 2 (default 2)
+};
+std::map<std::pair<int, int>, SegOpt> g_seg_opt;
+
+SegOpt resolve_seg_options(bool pairs, int nseg)
+{
+    int c = 0;
+    while ((1ll << c) < (long long)nseg) ++c;
+    SegOpt o;
+    auto it = g_seg_opt.find({pairs ? 1 : 0, c});
+    if (it != g_seg_opt.end()) o = it->second;
+    if (!o.tile_log2) o.tile_log2 = pairs ? 13 : 14;
+    if (!o.floor_gap) o.floor_gap = 10;
+    if (!o.ctas_per_sm) o.ctas_per_sm = 2;
+    return o;
+}
+
 // Per-size-class overrides set by the autotuner: (key bytes, log2 N) -> options.
 std::map<std::pair<int, int>, Options> g_class_opt;
 
@@ -116,7 +139,8 @@ struct DeviceState {
     int pipe_blocks[kNumTileCfgs] = {};  // resident pipelined CTAs per SM, per configuration
     int tile_blocks[kNumTileCfgs] = {};  // resident tile CTAs per SM, per configuration
     int* status = nullptr;               // device status word shared by every stream
-    TileParamsBig* seg_descs[2] = {nullptr, nullptr};  // packed segment tiles by class: keys, pairs
+    // packed segment tiles by class: 16K keys, 8K composites (pairs), 8K keys
+    TileParamsBig* seg_descs[3] = {nullptr, nullptr, nullptr};
     // Segments longer than one tile (keys): the launch plans of sorts of
     // 2^k keys, k = 15..31, built at the first segmented call.
     bool long_ready = false;
@@ -166,12 +190,12 @@ bitonic_status device_state(DeviceState** out)
         BT_CK(cudaStreamCreateWithFlags(&ds.capture, cudaStreamNonBlocking));
         BT_CK(cudaMalloc(&ds.status, sizeof(int)));
         BT_CK(cudaMemset(ds.status, 0, sizeof(int)));
-        for (int which = 0; which < 2; ++which) {
-            const int kb = which ? 8 : 4, m = which ? 13 : 14;
+        for (int which = 0; which < 3; ++which) {
+            const int kb = which == 1 ? 8 : 4, m = which == 0 ? 14 : 13;
             std::vector<TileParamsBig> descs(m + 1);
             std::memset(descs.data(), 0, descs.size() * sizeof(TileParamsBig));
             for (int k = 1; k <= m; ++k)
-                if (!make_class_desc(kb, k, descs[k])) return BITONIC_ERR_UNSUPPORTED;
+                if (!make_class_desc(kb, k, descs[k], m)) return BITONIC_ERR_UNSUPPORTED;
             BT_CK(cudaMalloc(&ds.seg_descs[which], descs.size() * sizeof(TileParamsBig)));
             BT_CK(cudaMemcpy(ds.seg_descs[which], descs.data(), descs.size() * sizeof(TileParamsBig),
                              cudaMemcpyHostToDevice));
@@ -182,8 +206,9 @@ bitonic_status device_state(DeviceState** out)
     return BITONIC_OK;
 }
 
-// Descriptors of the plain sorts of 2^k keys, k = m+1..31 (default options,
-// 16K-key tiles), for the long segments of a segmented batch.
+// Descriptors of the plain sorts of 2^k keys, k = 14..31 (default options,
+// 16K-key tiles), for the long segments of a segmented batch (k = 14, one
+// tile, only when the packed tiles hold 8K keys).
 bitonic_status ensure_long_plans(DeviceState& ds)
 {
     if (ds.long_ready) return BITONIC_OK;
@@ -191,7 +216,7 @@ bitonic_status ensure_long_plans(DeviceState& ds)
     lp.tile_log = 14;
     std::vector<TileParamsBig> descs;
     const Options o;
-    for (int k = lp.tile_log + 1; k <= 31; ++k) {
+    for (int k = lp.tile_log; k <= 31; ++k) {
         const Plan pl = make_plan(uint64_t(1) << k, 4, o);
         if (!pl.ok || pl.cfg != 0 || (int)pl.launches.size() > kLongMaxPasses) {
             t_last_error = "long-segment plans";
@@ -835,15 +860,18 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
     const size_t seg_need = vals ? seg_tiles_ws_bytes(nseg) : seg_long_ws_bytes(nseg);
     if ((st = stream_ws(*ds, s, 0, &w, seg_need))) return st;
     if (!vals && (st = ensure_long_plans(*ds))) return st;
-    // persistent packed-tile CTAs: as many as are resident
-    const int tile_grid = (vals ? kSegTileBlocksPairs : kSegTileBlocksKeys) * ds->num_sms;
+    const SegOpt so = resolve_seg_options(vals != nullptr, nseg);
+    const TileParamsBig* class_descs = vals ? ds->seg_descs[1] : ds->seg_descs[so.tile_log2 == 13 ? 2 : 0];
+    const uint64_t so_code = (uint64_t)so.tile_log2 << 16 | (uint64_t)so.floor_gap << 8 | (uint64_t)so.ctas_per_sm;
+    // persistent packed-tile CTAs: the chosen number resident per SM
+    const int tile_grid = so.ctas_per_sm * ds->num_sms;
     const int large_grid = 4 * ds->num_sms;
     if (!vals) {
-        GraphKey key{2, 0, 1, (uintptr_t)keys, 0, (uintptr_t)offsets, nseg, (uintptr_t)s, 0, 0, 0};
+        GraphKey key{2, 0, 1, (uintptr_t)keys, 0, (uintptr_t)offsets, nseg, (uintptr_t)s, 0, so_code, 0};
         void* ws = w->seg;
         return run_graphed(*ds, key, s, [&](cudaStream_t cs) -> bitonic_status {
-            BT_CK(seg_tiles_launch(keys, nullptr, offsets, nseg, ws, ds->seg_descs[0], tile_grid, ds->status,
-                                   debug_checks(), cs));
+            BT_CK(seg_tiles_launch(keys, nullptr, offsets, nseg, ws, class_descs, so.tile_log2, so.floor_gap,
+                                   tile_grid, ds->status, debug_checks(), cs));
             // segments longer than one tile: their own multi-pass plans, one persistent launch
             BT_CK(seg_long_launch(keys, offsets, nseg, ws, ds->long_plans, ds->long_descs,
                                   kSegTileBlocksKeys * ds->num_sms, ds->status, kLongWaitSpins, cs));
@@ -855,8 +883,8 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
     // caller bounds every segment by one tile.
     if (max_len >= 0 && max_len <= (1 << 13)) {
         void* ws = w->seg;
-        BT_CK(seg_tiles_launch(keys, vals, offsets, nseg, ws, ds->seg_descs[1], tile_grid, ds->status,
-                               debug_checks(), s));
+        BT_CK(seg_tiles_launch(keys, vals, offsets, nseg, ws, class_descs, 13, so.floor_gap, tile_grid,
+                               ds->status, debug_checks(), s));
         return BITONIC_OK;
     }
     if (stream_capturing(s)) {
@@ -870,8 +898,8 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
     size_t need = 0;
     if (longest > (1 << 13) && last > first) need = (size_t)(last - first);
     if ((st = stream_ws(*ds, s, need, &w, seg_need))) return st;
-    BT_CK(seg_tiles_launch(keys, vals, offsets, nseg, w->seg, ds->seg_descs[1], tile_grid, ds->status,
-                           debug_checks(), s));
+    BT_CK(seg_tiles_launch(keys, vals, offsets, nseg, w->seg, class_descs, 13, so.floor_gap, tile_grid,
+                           ds->status, debug_checks(), s));
     BT_CK(seg_launch_large(keys, vals, offsets, w->seg, w->comp, first, large_grid, s));
     return BITONIC_OK;
 }
@@ -1104,6 +1132,27 @@ bitonic_status bitonic_debug_set_wait(int starve_copies, unsigned max_spins)
     // a short bound only together with the starving mode: then no copy is in
     // flight when a wait gives up
     BT_CK(set_pipe_wait(starve_copies ? max_spins : 0u, starve_copies ? 1 : 0));
+    return BITONIC_OK;
+}
+
+bitonic_status bitonic_set_segmented_options(int pairs, int log2_nseg, const bitonic_seg_options* opt)
+{
+    if (log2_nseg < 0 || log2_nseg > 31) return BITONIC_ERR_INVALID;
+    std::lock_guard<std::mutex> g(g_mu);
+    const std::pair<int, int> key{pairs ? 1 : 0, log2_nseg};
+    if (!opt) {
+        g_seg_opt.erase(key);
+        return BITONIC_OK;
+    }
+    const bool tile_ok = opt->tile_log2 == 0 || opt->tile_log2 == 13 || (!pairs && opt->tile_log2 == 14);
+    if (!tile_ok || opt->class_floor_gap < 0 || opt->class_floor_gap > 10 || opt->ctas_per_sm < 0 ||
+        opt->ctas_per_sm > 2)
+        return BITONIC_ERR_INVALID;
+    SegOpt o;
+    o.tile_log2 = opt->tile_log2;
+    o.floor_gap = opt->class_floor_gap;
+    o.ctas_per_sm = opt->ctas_per_sm;
+    g_seg_opt[key] = o;
     return BITONIC_OK;
 }
 

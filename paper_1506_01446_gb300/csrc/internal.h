@@ -68,8 +68,8 @@ Plan make_plan(uint64_t n, int key_bytes, const Options& opt);
 const struct TileCfg& tile_cfg(int id);
 
 // Packed segmented tiles: descriptor for segments padded to 2^k positions
-// (key_bytes 4: 16K-key tile, 8: 8K-composite tile).
-bool make_class_desc(int key_bytes, int k, TileParamsBig& P);
+// (key_bytes 4: 16K-key or, tile_log2 = 13, 8K-key tile; 8: 8K-composite tile).
+bool make_class_desc(int key_bytes, int k, TileParamsBig& P, int tile_log2 = 14);
 
 // Launchers (kernels.cu).  Return the CUDA error of the launch.
 cudaError_t launch_pairs_pack(uint64_t* comp, const uint32_t* keys, uint32_t n, int desc,

@@ -487,12 +487,14 @@ bool to_small(const TileParamsBig& b, TileParams& s)
 const TileCfg& tile_cfg(int id) { return kCfgs[id]; }
 
 // Descriptor of a packed segmented tile whose segments are padded to 2^k
-// positions: phases 1..k of the network on a contiguous tile of the default
-// configuration (16K keys, or 8K composites for pairs).
-bool make_class_desc(int key_bytes, int k, TileParamsBig& P)
+// positions: phases 1..k of the network on a contiguous tile (16K or 8K
+// keys, or 8K composites for pairs).
+bool make_class_desc(int key_bytes, int k, TileParamsBig& P, int tile_log2)
 {
     std::memset(&P, 0, sizeof(P));
-    const int cfg_id = key_bytes == 4 ? 0 : 4;  // the packed segmented kernels use these two
+    // the packed segmented kernels: 16K keys (256 x 64) or 8K keys (256 x 32);
+    // 8K composites (256 x 32)
+    const int cfg_id = key_bytes == 4 ? (tile_log2 == 13 ? 1 : 0) : 4;
     const TileCfg& cfg = kCfgs[cfg_id];
     const int vb = key_bytes == 4 ? 2 : 1;
     const int m = cfg.log_r + cfg.log_t;

@@ -31,11 +31,12 @@ struct SegPlan {
     int pad_;
 };
 
-// Segments longer than one tile (keys only): each runs the full launch plan
-// of a sort of N = 2^k keys (its tile sort, multi-stride and merge passes),
-// k = ceil(log2(front + length)), front = the segment's offset from a 16-byte
-// boundary.  plans holds, per k, the number of launches and the index of the
-// first launch's descriptor in the device descriptor array.
+// Segments longer than one packed tile (keys only): each runs the full
+// launch plan of a sort of N = 2^k keys (its tile sort, multi-stride and
+// merge passes), k = ceil(log2(front + length)) >= tile_log, front = the
+// segment's offset from a 16-byte boundary.  plans holds, per k, the number
+// of launches and the index of the first launch's descriptor in the device
+// descriptor array.
 constexpr int kLongMaxPasses = 48;
 struct LongPlans {
     int npass[kSegClasses + 1];
@@ -69,8 +70,8 @@ cudaError_t seg_init_attributes();
 cudaError_t seg_tiles_init_attributes();
 size_t seg_tiles_ws_bytes(int nseg);
 cudaError_t seg_tiles_launch(uint32_t* keys, uint32_t* vals, const int32_t* offs, int nseg, void* ws,
-                             const TileParamsBig* class_descs, int grid, int* status, int debug_checks,
-                             cudaStream_t s);
+                             const TileParamsBig* class_descs, int m, int gap, int grid, int* status,
+                             int debug_checks, cudaStream_t s);
 // Segments of the large class (longer than one tile), one CTA each.
 cudaError_t seg_launch_large(uint32_t* keys, uint32_t* vals, const int32_t* offs, void* ws, uint64_t* comp,
                              int32_t comp_base, int grid, cudaStream_t s);

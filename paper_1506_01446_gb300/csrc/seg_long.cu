@@ -1,7 +1,8 @@
 // Segmented sort, segments longer than one tile (keys only).
 //
-// A segment of L keys whose first key lies `front` keys past a 16-byte boundary is the
-// sort of N = 2^k virtual positions (k = ceil(log2(front + L))) with its real
+// A segment of L keys whose first key lies `front` keys past a 16-byte
+// boundary is the sort of N = 2^k virtual positions (k = ceil(log2(front +
+// L)) >= 14; k = 14, a single tile, when the packed tiles hold 8K keys) with its real
 // keys in [front, front + L): the network of Section 3.1 split into the same
 // launches as a plain sort of N keys (tile sort, multi-stride passes, tile
 // merges; Sections 4.1 and 4.2), whose descriptors are built once per k.
@@ -83,7 +84,7 @@ __global__ void k_long_scan(LongSched* sched, const LongPlans plans)
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int m = plans.tile_log;
     int pos = 0;
-    for (int k = 31; k > m; --k) {
+    for (int k = 31; k >= m; --k) {
         sched->class_start[k] = pos;
         sched->cursor[k] = 0;
         pos += sched->count[k];
@@ -91,7 +92,7 @@ __global__ void k_long_scan(LongSched* sched, const LongPlans plans)
     int items = 0;
     for (int p = 0; p < kLongMaxPasses; ++p) {
         sched->pass_start[p] = items;
-        for (int k = 31; k > m; --k)
+        for (int k = 31; k >= m; --k)
             if (plans.npass[k] > p) items += sched->count[k] << (k - m);
     }
     sched->pass_start[kLongMaxPasses] = items;
@@ -155,7 +156,7 @@ k_long_sort(uint32_t* __restrict__ keys, const int32_t* __restrict__ offs, const
         while (item >= sched->pass_start[p + 1]) ++p;
         int o = item - sched->pass_start[p];
         int k = 31;
-        for (; k > m; --k) {
+        for (; k >= m; --k) {
             if (plans.npass[k] <= p) continue;
             const int sz = sched->count[k] << (k - m);
             if (o < sz) break;

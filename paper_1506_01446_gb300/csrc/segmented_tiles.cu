@@ -1,8 +1,8 @@
 // Batched segmented sort with packed tiles.
 //
 // Every segment of length L (2 <= L <= tile) belongs to size class
-// k = ceil(log2 L), raised to at least m - 10 so that a tile never holds more
-// than 1024 segments.  A tile of 2^m positions holds 2^(m-k) segments of one
+// k = ceil(log2 L), raised to at least m - gap (gap <= 10: a tile never holds
+// more than 1024 segments; the autotuner picks the gap and the tile size).  A tile of 2^m positions holds 2^(m-k) segments of one
 // class, each padded (virtually) to 2^k positions, and the tile engine runs
 // phases 1..k of the network on it (Sections 3.1, 4.1, 4.2): those phases
 // never mix positions of different 2^k blocks, so each segment is sorted on
@@ -22,15 +22,15 @@ namespace {
 
 constexpr int kSegTileThreads = 256;
 
-__device__ __forceinline__ int seg_class(int32_t len, int m)
+__device__ __forceinline__ int seg_class(int32_t len, int m, int gap)
 {
     if (len < 2) return kSegClassSkip;
     if (len > (1 << m)) return kSegClassLarge;
     int k = 32 - __clz((uint32_t)(len - 1));  // ceil(log2 len)
-    return k < m - 10 ? m - 10 : k;
+    return k < m - gap ? m - gap : k;
 }
 
-__global__ void k_seg_classify(const int32_t* __restrict__ offs, int nseg, int m, uint8_t* __restrict__ cls,
+__global__ void k_seg_classify(const int32_t* __restrict__ offs, int nseg, int m, int gap, uint8_t* __restrict__ cls,
                                SegPlan* plan, int* status, int debug_checks)
 {
     __shared__ int hist[kSegClasses];
@@ -39,7 +39,7 @@ __global__ void k_seg_classify(const int32_t* __restrict__ offs, int nseg, int m
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
         const int32_t len = offs[s + 1] - offs[s];
         if (len < 0 && debug_checks) atomicCAS(status, 0, 1);
-        const int c = seg_class(len, m);
+        const int c = seg_class(len, m, gap);
         cls[s] = (uint8_t)c;
         atomicAdd(&hist[c], 1);
     }
@@ -217,6 +217,9 @@ cudaError_t seg_tiles_init_attributes()
         e = cudaFuncSetAttribute(k_seg_tiles<uint32_t, 6, 8, kSegTileBlocksKeys>,
                                  cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_seg_tiles<uint32_t, 5, 8, kSegTileBlocksKeys>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_tile_smem<uint32_t, 5, 8>());
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_seg_tiles<uint64_t, 5, 8, kSegTileBlocksPairs>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_tile_smem<uint64_t, 5, 8>());
     return e;
@@ -224,12 +227,14 @@ cudaError_t seg_tiles_init_attributes()
 
 // Enqueues classify, scan, scatter and the packed tile sort.  ws must hold
 // SegPlan, nseg class bytes and nseg order entries (seg_tiles_ws_bytes).
+// Tiles of 2^m keys (keys: m = 14, 256 threads x 64, or 13, 256 x 32; pairs:
+// 8K composites, m = 13); the smallest class is m - gap.
 cudaError_t seg_tiles_launch(uint32_t* keys, uint32_t* vals, const int32_t* offs, int nseg, void* ws,
-                             const TileParamsBig* class_descs, int grid, int* status, int debug_checks,
-                             cudaStream_t s)
+                             const TileParamsBig* class_descs, int m, int gap, int grid, int* status,
+                             int debug_checks, cudaStream_t s)
 {
     const bool pairs = vals != nullptr;
-    const int m = pairs ? 13 : 14;
+    if ((pairs && m != 13) || (!pairs && m != 13 && m != 14) || gap < 1 || gap > 10) return cudaErrorInvalidValue;
     SegPlan* plan = reinterpret_cast<SegPlan*>(ws);
     int32_t* order = reinterpret_cast<int32_t*>(plan + 1);
     uint8_t* cls = reinterpret_cast<uint8_t*>(order + nseg);
@@ -237,14 +242,17 @@ cudaError_t seg_tiles_launch(uint32_t* keys, uint32_t* vals, const int32_t* offs
     if (e != cudaSuccess) return e;
     int cgrid = (nseg + 255) / 256;
     cgrid = cgrid < 1 ? 1 : (cgrid > 1024 ? 1024 : cgrid);
-    k_seg_classify<<<cgrid, 256, 0, s>>>(offs, nseg, m, cls, plan, status, debug_checks);
+    k_seg_classify<<<cgrid, 256, 0, s>>>(offs, nseg, m, gap, cls, plan, status, debug_checks);
     k_seg_scan<<<1, 32, 0, s>>>(plan, m);
     k_seg_scatter<<<cgrid, 256, 0, s>>>(cls, nseg, plan, order);
     if (pairs)
         k_seg_tiles<uint64_t, 5, 8, kSegTileBlocksPairs><<<grid, kSegTileThreads, seg_tile_smem<uint64_t, 5, 8>(), s>>>(
             keys, vals, offs, order, plan, class_descs, &plan->tile_counter);
-    else
+    else if (m == 14)
         k_seg_tiles<uint32_t, 6, 8, kSegTileBlocksKeys><<<grid, kSegTileThreads, seg_tile_smem<uint32_t, 6, 8>(), s>>>(
+            keys, nullptr, offs, order, plan, class_descs, &plan->tile_counter);
+    else
+        k_seg_tiles<uint32_t, 5, 8, kSegTileBlocksKeys><<<grid, kSegTileThreads, seg_tile_smem<uint32_t, 5, 8>(), s>>>(
             keys, nullptr, offs, order, plan, class_descs, &plan->tile_counter);
     return cudaGetLastError();
 }

@@ -250,13 +250,14 @@ class SortServer:
             for stream in self.streams:
                 sh = stream.cuda_stream
                 with torch.cuda.stream(stream):
-                    n = 1 << 10
-                    while n <= n_max:
+                    # every power of two up to the largest request, and the
+                    # largest itself (its plan and its workspace size)
+                    ns = [1 << j for j in range(10, 32) if (1 << j) <= n_max] + [n_max]
+                    for n in ns:
                         for st in (self.lib.bitonic_sort_u32(k.data_ptr(), n, 1, sh),
                                    self.lib.bitonic_sort_pairs_u32(k.data_ptr(), v.data_ptr(), n, 1, sh)):
                             if st != OK:
                                 raise RuntimeError(status_string(st))
-                        n <<= 1
                     for st in (self.lib.bitonic_sort_segmented_u32(k.data_ptr(), offs.data_ptr(), nb, sh),
                                self.lib.bitonic_sort_segmented_pairs_u32_bounded(
                                    k.data_ptr(), v.data_ptr(), offs.data_ptr(), nb, self.small_pairs, sh)):
