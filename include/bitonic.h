@@ -178,12 +178,14 @@ bitonic_status bitonic_sort_segmented_u32(uint32_t *keys, const int32_t *offsets
 
 /* Segmented key/value sort: each segment sorted ascending by (key, index)
  * with its values, as bitonic_sort_pairs_u32 does for one array.  Segments
- * of up to 8192 pairs are packed into tiles of 64-bit composites; a longer
- * segment is sorted by one CTA running the network on composites in global
- * memory.  When a segment may exceed 8192 pairs the call reads three ints
- * back (the offsets' span and the longest segment, one stream
- * synchronisation) to size the composite workspace, so it cannot be
- * captured; bitonic_sort_segmented_pairs_u32_bounded avoids the read-back. */
+ * of up to 8192 pairs are packed into tiles of 64-bit composites; each
+ * longer segment runs the launch plan of a 2^k composite sort in a shared
+ * persistent launch (as the keys-only call does), with a pack pass before it
+ * and gather and split passes after it, its composites in a workspace sized
+ * by the span of the offsets.  To size that workspace the call reads three
+ * ints back (the offsets' span and the longest segment, one stream
+ * synchronisation), so it cannot be captured;
+ * bitonic_sort_segmented_pairs_u32_bounded avoids the read-back. */
 bitonic_status bitonic_sort_segmented_pairs_u32(uint32_t *keys, uint32_t *vals,
                                                 const int32_t *offsets, int nseg,
                                                 bitonic_stream_t stream);

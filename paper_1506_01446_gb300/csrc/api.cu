@@ -143,9 +143,9 @@ struct DeviceState {
     TileParamsBig* seg_descs[3] = {nullptr, nullptr, nullptr};
     // Segments longer than one tile (keys): the launch plans of sorts of
     // 2^k keys, k = 15..31, built at the first segmented call.
-    bool long_ready = false;
-    LongPlans long_plans = {};
-    TileParamsBig* long_descs = nullptr;
+    bool long_ready[2] = {false, false};  // keys, pairs
+    LongPlans long_plans[2] = {};
+    TileParamsBig* long_descs[2] = {nullptr, nullptr};
     std::map<cudaStream_t, StreamWs> ws;
     std::map<PlanKey, std::unique_ptr<PlanEntry>> plans;
     std::map<GraphKey, GraphEntry> graphs;
@@ -206,23 +206,26 @@ bitonic_status device_state(DeviceState** out)
     return BITONIC_OK;
 }
 
-// Descriptors of the plain sorts of 2^k keys, k = 14..31 (default options,
-// 16K-key tiles), for the long segments of a segmented batch (k = 14, one
-// tile, only when the packed tiles hold 8K keys).
-bitonic_status ensure_long_plans(DeviceState& ds)
+// Descriptors of the plain sorts of 2^k keys, k = m..31 (default options),
+// for the long segments of a segmented batch: keys (pairs = 0) on 16K-key
+// tiles, m = 14 (k = 14, one tile, only when the packed tiles hold 8K keys);
+// pairs on 8K-composite tiles, m = 13, whose schedules add a pack pass
+// before the plan and gather and split passes after it.
+bitonic_status ensure_long_plans(DeviceState& ds, int pairs)
 {
-    if (ds.long_ready) return BITONIC_OK;
+    if (ds.long_ready[pairs]) return BITONIC_OK;
     LongPlans lp = {};
-    lp.tile_log = 14;
+    lp.tile_log = pairs ? 13 : 14;
+    const int extra = pairs ? 3 : 0;
     std::vector<TileParamsBig> descs;
     const Options o;
     for (int k = lp.tile_log; k <= 31; ++k) {
-        const Plan pl = make_plan(uint64_t(1) << k, 4, o);
-        if (!pl.ok || pl.cfg != 0 || (int)pl.launches.size() > kLongMaxPasses) {
+        const Plan pl = make_plan(uint64_t(1) << k, pairs ? 8 : 4, o);
+        if (!pl.ok || pl.cfg != (pairs ? 4 : 0) || (int)pl.launches.size() + extra > kLongMaxPasses) {
             t_last_error = "long-segment plans";
             return BITONIC_ERR_UNSUPPORTED;
         }
-        lp.npass[k] = (int)pl.launches.size();
+        lp.npass[k] = (int)pl.launches.size() + extra;
         lp.desc0[k] = (int)descs.size();
         for (const Launch& L : pl.launches) {
             if (L.desc < 0 || L.grid != (1u << (k - lp.tile_log))) {
@@ -233,10 +236,10 @@ bitonic_status ensure_long_plans(DeviceState& ds)
         }
     }
     const size_t bytes = descs.size() * sizeof(TileParamsBig);
-    BT_CK(cudaMalloc(&ds.long_descs, bytes));
-    BT_CK(cudaMemcpy(ds.long_descs, descs.data(), bytes, cudaMemcpyHostToDevice));
-    ds.long_plans = lp;
-    ds.long_ready = true;
+    BT_CK(cudaMalloc(&ds.long_descs[pairs], bytes));
+    BT_CK(cudaMemcpy(ds.long_descs[pairs], descs.data(), bytes, cudaMemcpyHostToDevice));
+    ds.long_plans[pairs] = lp;
+    ds.long_ready[pairs] = true;
     return BITONIC_OK;
 }
 
@@ -857,15 +860,14 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
     DeviceState* ds;
     if ((st = device_state(&ds))) return st;
     StreamWs* w;
-    const size_t seg_need = vals ? seg_tiles_ws_bytes(nseg) : seg_long_ws_bytes(nseg);
+    const size_t seg_need = seg_long_ws_bytes(nseg);
     if ((st = stream_ws(*ds, s, 0, &w, seg_need))) return st;
-    if (!vals && (st = ensure_long_plans(*ds))) return st;
+    if ((st = ensure_long_plans(*ds, vals ? 1 : 0))) return st;
     const SegOpt so = resolve_seg_options(vals != nullptr, nseg);
     const TileParamsBig* class_descs = vals ? ds->seg_descs[1] : ds->seg_descs[so.tile_log2 == 13 ? 2 : 0];
     const uint64_t so_code = (uint64_t)so.tile_log2 << 16 | (uint64_t)so.floor_gap << 8 | (uint64_t)so.ctas_per_sm;
     // persistent packed-tile CTAs: the chosen number resident per SM
     const int tile_grid = so.ctas_per_sm * ds->num_sms;
-    const int large_grid = 4 * ds->num_sms;
     if (!vals) {
         GraphKey key{2, 0, 1, (uintptr_t)keys, 0, (uintptr_t)offsets, nseg, (uintptr_t)s, 0, so_code, 0};
         void* ws = w->seg;
@@ -873,7 +875,8 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
             BT_CK(seg_tiles_launch(keys, nullptr, offsets, nseg, ws, class_descs, so.tile_log2, so.floor_gap,
                                    tile_grid, ds->status, debug_checks(), cs));
             // segments longer than one tile: their own multi-pass plans, one persistent launch
-            BT_CK(seg_long_launch(keys, offsets, nseg, ws, ds->long_plans, ds->long_descs,
+            BT_CK(seg_long_launch(LongIo{keys, nullptr, nullptr, 0}, offsets, nseg, ws, ds->long_plans[0],
+                                  ds->long_descs[0],
                                   kSegTileBlocksKeys * ds->num_sms, ds->status, kLongWaitSpins, cs));
             return BITONIC_OK;
         });
@@ -900,7 +903,11 @@ bitonic_status sort_segmented_impl(uint32_t* keys, uint32_t* vals, const int32_t
     if ((st = stream_ws(*ds, s, need, &w, seg_need))) return st;
     BT_CK(seg_tiles_launch(keys, vals, offsets, nseg, w->seg, class_descs, 13, so.floor_gap, tile_grid,
                            ds->status, debug_checks(), s));
-    BT_CK(seg_launch_large(keys, vals, offsets, w->seg, w->comp, first, large_grid, s));
+    // segments longer than one tile: composites in the workspace at their
+    // offset from offsets[0], their own multi-pass plans, one persistent launch
+    if (longest > (1 << 13))
+        BT_CK(seg_long_launch(LongIo{keys, vals, w->comp, first}, offsets, nseg, w->seg, ds->long_plans[1],
+                              ds->long_descs[1], kSegTileBlocksPairs * ds->num_sms, ds->status, kLongWaitSpins, s));
     return BITONIC_OK;
 }
 

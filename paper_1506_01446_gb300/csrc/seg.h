@@ -31,17 +31,28 @@ struct SegPlan {
     int pad_;
 };
 
-// Segments longer than one packed tile (keys only): each runs the full
-// launch plan of a sort of N = 2^k keys (its tile sort, multi-stride and
-// merge passes), k = ceil(log2(front + length)) >= tile_log, front = the
-// segment's offset from a 16-byte boundary.  plans holds, per k, the number
-// of launches and the index of the first launch's descriptor in the device
+// Segments longer than one packed tile: each runs the full launch plan of a
+// sort of N = 2^k keys (its tile sort, multi-stride and merge passes),
+// k = ceil(log2(front + length)) >= tile_log, front = the segment's offset
+// from a 16-byte boundary.  plans holds, per k, the number of passes of the
+// segment's schedule (for pairs the plan's launches plus pack, gather and
+// split) and the index of the plan's first descriptor in the device
 // descriptor array.
 constexpr int kLongMaxPasses = 48;
 struct LongPlans {
     int npass[kSegClasses + 1];
     int desc0[kSegClasses + 1];
-    int tile_log;  // m: log2 keys per tile of the plans
+    int tile_log;  // m: log2 keys per tile of the plans (14 keys, 13 composites)
+};
+
+// Arrays of a long-segment launch.  Keys: the tiles run on keys.  Pairs
+// (vals != NULL): on 64-bit composites, that of position p (an index into
+// keys) at comp[p - comp_first].
+struct LongIo {
+    uint32_t* keys;
+    uint32_t* vals;
+    uint64_t* comp;
+    int32_t comp_first;
 };
 
 // Device-side schedule of one batch's long segments (built per call).
@@ -62,7 +73,7 @@ cudaError_t seg_long_init_attributes();
 // Sorts the batch's long segments (the packed-tile launch's large class,
 // listed in ws) with one persistent launch; max_spins bounds each wait for a
 // segment's previous pass.
-cudaError_t seg_long_launch(uint32_t* keys, const int32_t* offs, int nseg, void* ws, const LongPlans& plans,
+cudaError_t seg_long_launch(const LongIo& io, const int32_t* offs, int nseg, void* ws, const LongPlans& plans,
                             const TileParamsBig* descs, int grid, int* status, uint32_t max_spins,
                             cudaStream_t s);
 
@@ -72,9 +83,6 @@ size_t seg_tiles_ws_bytes(int nseg);
 cudaError_t seg_tiles_launch(uint32_t* keys, uint32_t* vals, const int32_t* offs, int nseg, void* ws,
                              const TileParamsBig* class_descs, int m, int gap, int grid, int* status,
                              int debug_checks, cudaStream_t s);
-// Segments of the large class (longer than one tile), one CTA each.
-cudaError_t seg_launch_large(uint32_t* keys, uint32_t* vals, const int32_t* offs, void* ws, uint64_t* comp,
-                             int32_t comp_base, int grid, cudaStream_t s);
 // out[0] = offsets[0], out[1] = offsets[nseg], out[2] = longest segment.
 cudaError_t seg_launch_stats(const int32_t* offs, int nseg, int* out, cudaStream_t s);
 // keys[i] = ~keys[i] for i in [offsets[0], offsets[nseg]) (grid-stride).

@@ -1,14 +1,20 @@
-// Segmented sort, segments longer than one tile (keys only).
+// Segmented sort: segments longer than one packed tile.
 //
-// A segment of L keys whose first key lies `front` keys past a 16-byte
-// boundary is the sort of N = 2^k virtual positions (k = ceil(log2(front +
-// L)) >= 14; k = 14, a single tile, when the packed tiles hold 8K keys) with its real
-// keys in [front, front + L): the network of Section 3.1 split into the same
+// A segment of L keys whose first element lies `front` elements past a
+// 16-byte boundary is the sort of N = 2^k virtual positions (k =
+// ceil(log2(front + L)), at least the tile size) with its real elements in
+// [front, front + L): the network of Section 3.1 split into the same
 // launches as a plain sort of N keys (tile sort, multi-stride passes, tile
 // merges; Sections 4.1 and 4.2), whose descriptors are built once per k.
+// Key sorts run on the caller's keys.  Pair sorts run on 64-bit composites
+// (key << 32) | index-in-segment in a workspace, with three more passes per
+// segment: pack (build the composites), gather (read each value by the
+// composite's index into its low half) and split (write keys and values
+// back); equal keys keep their original order.
+//
 // All of a batch's long segments run in one persistent launch: work items
 // (pass p, segment, tile t) are numbered pass by pass and taken from an
-// atomic counter, and a tile of pass p first waits until every tile of pass
+// atomic counter, and an item of pass p first waits until every tile of pass
 // p - 1 of its segment is done (a per-segment counter of finished tiles).
 // A CTA only waits for items that running CTAs took earlier, so the launch
 // always makes progress; every wait is bounded and reports a timeout in the
@@ -26,12 +32,22 @@ namespace bitonic {
 namespace {
 
 constexpr int kLongThreads = 256;
-constexpr int kLongLogR = 6;  // the 4-byte default tile: 256 threads x 64 keys
-constexpr int kLongLogT = 8;
 constexpr int kLongBlocks = 2;
-constexpr int kLongM = kLongLogR + kLongLogT;
 constexpr int kDevTimeoutCode = 2;  // device status word: a wait gave up
 constexpr int kDevTooLongCode = 1;  // a segment longer than the library's maximum sort
+
+// Tile shape of the long-segment kernels: 4-byte keys as 256 threads x 64
+// (16K-key tiles), composites as 256 threads x 32 (8K composites).
+template <typename K>
+struct LongShape;
+template <>
+struct LongShape<uint32_t> {
+    static constexpr int LOG_R = 6, LOG_T = 8;
+};
+template <>
+struct LongShape<uint64_t> {
+    static constexpr int LOG_R = 5, LOG_T = 8;
+};
 
 __device__ __forceinline__ int ceil_log2_u64(uint64_t v)
 {
@@ -48,27 +64,40 @@ __device__ __forceinline__ void long_list(const SegPlan* plan, const int32_t* or
     *n = plan->hist[kSegClassLarge];
 }
 
-// Keys between a segment's first key and the 16-byte boundary below it.
-__device__ __forceinline__ uint32_t seg_front(const uint32_t* keys, int32_t start)
+// The array a segment's tiles run on (elements of K), at its first element.
+template <typename K>
+__device__ __forceinline__ K* seg_array(const LongIo& io, int32_t start)
 {
-    return (uint32_t)(((uintptr_t)(keys + start) & 15u) >> 2);
+    if constexpr (sizeof(K) == 8)
+        return reinterpret_cast<K*>(io.comp) + (start - io.comp_first);
+    else
+        return reinterpret_cast<K*>(io.keys) + start;
 }
 
-__device__ __forceinline__ int long_class(const uint32_t* keys, const int32_t* offs, int s)
+// Elements between a segment's first element and the 16-byte boundary below it.
+template <typename K>
+__device__ __forceinline__ uint32_t seg_front(const LongIo& io, int32_t start)
+{
+    return (uint32_t)(((uintptr_t)seg_array<K>(io, start) & 15u) / sizeof(K));
+}
+
+template <typename K>
+__device__ __forceinline__ int long_class(const LongIo& io, const int32_t* offs, int s)
 {
     const int32_t start = offs[s];
-    const uint64_t v = (uint64_t)seg_front(keys, start) + (uint64_t)(offs[s + 1] - start);
+    const uint64_t v = (uint64_t)seg_front<K>(io, start) + (uint64_t)(offs[s + 1] - start);
     return ceil_log2_u64(v);
 }
 
-__global__ void k_long_classify(const uint32_t* keys, const int32_t* __restrict__ offs, const SegPlan* __restrict__ plan,
+template <typename K>
+__global__ void k_long_classify(const LongIo io, const int32_t* __restrict__ offs, const SegPlan* __restrict__ plan,
                                 const int32_t* __restrict__ order, LongSched* sched, int* status)
 {
     const int32_t* list;
     int n;
     long_list(plan, order, &list, &n);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int k = long_class(keys, offs, list[i]);
+        const int k = long_class<K>(io, offs, list[i]);
         if (k > 31) {
             atomicCAS(status, 0, kDevTooLongCode);
             continue;
@@ -100,7 +129,8 @@ __global__ void k_long_scan(LongSched* sched, const LongPlans plans)
     sched->work = 0;
 }
 
-__global__ void k_long_scatter(const uint32_t* keys, const int32_t* __restrict__ offs, const SegPlan* __restrict__ plan,
+template <typename K>
+__global__ void k_long_scatter(const LongIo io, const int32_t* __restrict__ offs, const SegPlan* __restrict__ plan,
                                const int32_t* __restrict__ order, LongSched* sched, int32_t* __restrict__ slots,
                                int32_t* __restrict__ done)
 {
@@ -109,7 +139,7 @@ __global__ void k_long_scatter(const uint32_t* keys, const int32_t* __restrict__
     long_list(plan, order, &list, &n);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int s = list[i];
-        const int k = long_class(keys, offs, s);
+        const int k = long_class<K>(io, offs, s);
         if (k > 31) continue;
         const int slot = sched->class_start[k] + atomicAdd(&sched->cursor[k], 1);
         slots[slot] = s;
@@ -129,19 +159,31 @@ __device__ __forceinline__ bool wait_count(const int32_t* ctr, int need, uint32_
     }
 }
 
-// Shared memory: the tile, then the descriptor of the item's launch.
-constexpr size_t kLongTileBytes = (size_t(1) << kLongM) * sizeof(uint32_t);
-constexpr size_t kLongSmem = kLongTileBytes + sizeof(TileParamsBig);
-
-__global__ void __launch_bounds__(kLongThreads, kLongBlocks)
-k_long_sort(uint32_t* __restrict__ keys, const int32_t* __restrict__ offs, const int32_t* __restrict__ slots,
-            int32_t* done, LongSched* sched, const LongPlans plans, const TileParamsBig* __restrict__ descs,
-            int* status, uint32_t max_spins)
+template <typename K>
+constexpr size_t long_tile_bytes()
 {
-    using T = Tile<uint32_t, false, kLongLogR, kLongLogT>;
+    return (size_t(1) << (LongShape<K>::LOG_R + LongShape<K>::LOG_T)) * sizeof(K);
+}
+
+// Shared memory: the tile, then the descriptor of the item's launch.
+template <typename K>
+constexpr size_t long_smem()
+{
+    return long_tile_bytes<K>() + sizeof(TileParamsBig);
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kLongThreads, kLongBlocks)
+k_long_sort(const LongIo io, const int32_t* __restrict__ offs, const int32_t* __restrict__ slots, int32_t* done,
+            LongSched* sched, const LongPlans plans, const TileParamsBig* __restrict__ descs, int* status,
+            uint32_t max_spins)
+{
+    constexpr int LOG_R = LongShape<K>::LOG_R, LOG_T = LongShape<K>::LOG_T;
+    constexpr bool kPairs = sizeof(K) == 8;
+    using T = Tile<K, false, LOG_R, LOG_T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto* sm = reinterpret_cast<T::Vec*>(smem_raw);
-    auto* P = reinterpret_cast<TileParamsBig*>(smem_raw + kLongTileBytes);
+    auto* sm = reinterpret_cast<typename T::Vec*>(smem_raw);
+    auto* P = reinterpret_cast<TileParamsBig*>(smem_raw + long_tile_bytes<K>());
     __shared__ int s_item;
     const uint32_t x = threadIdx.x;
     const int m = plans.tile_log;
@@ -167,14 +209,19 @@ k_long_sort(uint32_t* __restrict__ keys, const int32_t* __restrict__ offs, const
         const uint32_t t = (uint32_t)o & ((1u << tl) - 1u);
         const int s = slots[slot];
         const int32_t start = offs[s];
-        const uint32_t front = seg_front(keys, start);
-        const uint32_t hi = front + (uint32_t)(offs[s + 1] - start);
-        uint32_t* base = keys + (start - (int32_t)front);
-        // every tile of this segment's previous launch must be done
+        const uint32_t len = (uint32_t)(offs[s + 1] - start);
+        const uint32_t front = seg_front<K>(io, start);
+        const uint32_t hi = front + len;
+        K* base = seg_array<K>(io, start) - front;  // virtual position 0 of the segment's sort
+        // every tile of this segment's previous pass must be done
         if (x == 0 && p > 0 && !wait_count(done + slot, p << tl, max_spins)) atomicCAS(status, 0, kDevTimeoutCode);
-        // the launch's descriptor (header and its rounds) into shared memory
-        {
-            const TileParamsBig* D = descs + plans.desc0[k] + p;
+        const int np = plans.npass[k];
+        // pair segments: pass 0 packs, the last two gather and split; the
+        // plan's launches are passes 1 .. np - 3
+        const int plan_pass = kPairs ? p - 1 : p;
+        const bool plan_item = !kPairs || (p >= 1 && p <= np - 3);
+        if (plan_item) {  // the launch's descriptor (header and its rounds) into shared memory
+            const TileParamsBig* D = descs + plans.desc0[k] + plan_pass;
             const int words = (int)((offsetof(TileParamsBig, rounds) + D->nrounds * sizeof(RoundDesc)) / 4);
             const uint32_t* src = reinterpret_cast<const uint32_t*>(D);
             uint32_t* dst = reinterpret_cast<uint32_t*>(P);
@@ -182,25 +229,77 @@ k_long_sort(uint32_t* __restrict__ keys, const int32_t* __restrict__ offs, const
         }
         __threadfence();
         __syncthreads();
-        const uint32_t g0 = cta_base(*P, t);
-        if (!(P->contiguous && g0 >= hi)) {
-            const bool interior = (g0 & ~P->span_mask) >= front && (g0 | P->span_mask) < hi;
-            const KeyMap<uint32_t> ident{0u, 0u, 0u};
-            T tile;
-            if (interior)
-                tile.load_global_interior<true>(base, P->io[0], g0, x, ident);
-            else
-                tile.load_global<true>(base, front, hi, P->io[0], g0, x, ident);
-            run_tile_rounds<uint32_t, false, kLongLogR, kLongLogT, true>(tile, sm, *P, x);
-            if (interior)
-                tile.store_global_interior(base, P->io[1], g0, x, ident);
-            else
-                tile.store_global(base, front, hi, P->io[1], g0, x, ident);
+        if (plan_item) {
+            const uint32_t g0 = cta_base(*P, t);
+            if (!(P->contiguous && g0 >= hi)) {
+                const bool interior = (g0 & ~P->span_mask) >= front && (g0 | P->span_mask) < hi;
+                const KeyMap<K> ident{K(0), K(0), K(0)};
+                T tile;
+                if (interior)
+                    tile.template load_global_interior<true>(base, P->io[0], g0, x, ident);
+                else
+                    tile.template load_global<true>(base, front, hi, P->io[0], g0, x, ident);
+                run_tile_rounds<K, false, LOG_R, LOG_T, !kPairs>(tile, sm, *P, x);
+                if (interior)
+                    tile.store_global_interior(base, P->io[1], g0, x, ident);
+                else
+                    tile.store_global(base, front, hi, P->io[1], g0, x, ident);
+            }
+        } else if constexpr (kPairs) {
+            // chunk t of the segment's virtual positions, real ones only
+            const uint32_t q0 = max(t << m, front), q1 = min((t + 1) << m, hi);
+            uint32_t* sk = io.keys + start;
+            uint32_t* sv = io.vals + start;
+            for (uint32_t q = q0 + x; q < q1; q += kLongThreads) {
+                const uint32_t j = q - front;  // index in the segment
+                if (p == 0) {
+                    base[q] = ((uint64_t)sk[j] << 32) | j;
+                } else if (p == np - 2) {  // values stay unchanged until the split pass
+                    const uint64_t c = __ldcg(base + q);
+                    base[q] = (c & 0xFFFFFFFF00000000ull) | sv[(uint32_t)c];
+                } else {
+                    const uint64_t c = __ldcg(base + q);
+                    sk[j] = (uint32_t)(c >> 32);
+                    sv[j] = (uint32_t)c;
+                }
+            }
         }
         __threadfence();
         __syncthreads();  // stores done; shared memory and s_item free for the next item
         if (x == 0) atomicAdd(done + slot, 1);
     }
+}
+
+template <typename K>
+cudaError_t long_attr()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_long_sort<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)long_smem<K>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_long_sort<K>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+}
+
+template <typename K>
+cudaError_t long_launch(const LongIo& io, const int32_t* offs, int nseg, void* ws, const LongPlans& plans,
+                        const TileParamsBig* descs, int grid, int* status, uint32_t max_spins, cudaStream_t s)
+{
+    if (plans.tile_log != LongShape<K>::LOG_R + LongShape<K>::LOG_T) return cudaErrorInvalidValue;
+    const SegPlan* plan = reinterpret_cast<const SegPlan*>(ws);
+    const int32_t* order = reinterpret_cast<const int32_t*>(plan + 1);
+    LongSched* sched = reinterpret_cast<LongSched*>(reinterpret_cast<char*>(ws) + seg_long_ws_offset(nseg));
+    int32_t* slots = reinterpret_cast<int32_t*>(sched + 1);
+    int32_t* done = slots + nseg;
+    cudaError_t e = cudaMemsetAsync(sched, 0, sizeof(LongSched), s);
+    if (e != cudaSuccess) return e;
+    int cgrid = (nseg + 255) / 256;
+    cgrid = cgrid < 1 ? 1 : (cgrid > 1024 ? 1024 : cgrid);
+    k_long_classify<K><<<cgrid, 256, 0, s>>>(io, offs, plan, order, sched, status);
+    k_long_scan<<<1, 32, 0, s>>>(sched, plans);
+    k_long_scatter<K><<<cgrid, 256, 0, s>>>(io, offs, plan, order, sched, slots, done);
+    k_long_sort<K><<<grid, kLongThreads, long_smem<K>(), s>>>(io, offs, slots, done, sched, plans, descs, status,
+                                                             max_spins);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -214,29 +313,17 @@ size_t seg_long_ws_bytes(int nseg)
 
 cudaError_t seg_long_init_attributes()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_long_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_long_sort, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaError_t e = long_attr<uint32_t>();
+    if (e == cudaSuccess) e = long_attr<uint64_t>();
     return e;
 }
 
-cudaError_t seg_long_launch(uint32_t* keys, const int32_t* offs, int nseg, void* ws, const LongPlans& plans,
+cudaError_t seg_long_launch(const LongIo& io, const int32_t* offs, int nseg, void* ws, const LongPlans& plans,
                             const TileParamsBig* descs, int grid, int* status, uint32_t max_spins, cudaStream_t s)
 {
-    if (plans.tile_log != kLongM) return cudaErrorInvalidValue;
-    const SegPlan* plan = reinterpret_cast<const SegPlan*>(ws);
-    const int32_t* order = reinterpret_cast<const int32_t*>(plan + 1);
-    LongSched* sched = reinterpret_cast<LongSched*>(reinterpret_cast<char*>(ws) + seg_long_ws_offset(nseg));
-    int32_t* slots = reinterpret_cast<int32_t*>(sched + 1);
-    int32_t* done = slots + nseg;
-    cudaError_t e = cudaMemsetAsync(sched, 0, sizeof(LongSched), s);
-    if (e != cudaSuccess) return e;
-    int cgrid = (nseg + 255) / 256;
-    cgrid = cgrid < 1 ? 1 : (cgrid > 1024 ? 1024 : cgrid);
-    k_long_classify<<<cgrid, 256, 0, s>>>(keys, offs, plan, order, sched, status);
-    k_long_scan<<<1, 32, 0, s>>>(sched, plans);
-    k_long_scatter<<<cgrid, 256, 0, s>>>(keys, offs, plan, order, sched, slots, done);
-    k_long_sort<<<grid, kLongThreads, kLongSmem, s>>>(keys, offs, slots, done, sched, plans, descs, status, max_spins);
-    return cudaGetLastError();
+    if (io.vals)
+        return long_launch<uint64_t>(io, offs, nseg, ws, plans, descs, grid, status, max_spins, s);
+    return long_launch<uint32_t>(io, offs, nseg, ws, plans, descs, grid, status, max_spins, s);
 }
 
 }  // namespace bitonic

@@ -1,9 +1,6 @@
-// Segmented sort of pairs: segments longer than one tile, and the batch
-// statistics used to size the pair workspace.  Each long pair segment is
-// sorted by one CTA running the network of Section 3.1 (mirror form) on
-// global memory with block barriers between steps; persistent CTAs pull
-// segments from an atomic counter.  (Long keys-only segments run their
-// multi-pass plans instead: seg_long.cu.)
+// Segmented sort helpers: the batch statistics that size the pair workspace,
+// and the key complement of the descending sorts.  (Segments longer than
+// one tile run their multi-pass plans: seg_long.cu.)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -12,82 +9,6 @@
 namespace bitonic {
 
 namespace {
-
-constexpr int kSegThreads = 256;
-
-__device__ __forceinline__ uint32_t next_pow2_u32(uint32_t v)
-{
-    uint32_t N = 1;
-    while (N < v) N <<= 1;
-    return N;
-}
-
-__device__ __forceinline__ int log2_u32(uint32_t N)
-{
-    return 31 - __clz(N);
-}
-
-// Same network on global memory with virtual padding (partner >= len is a
-// no-op).  One CTA; __syncthreads orders its global accesses.
-template <typename K>
-__device__ void global_network(K* a, uint32_t len)
-{
-    const uint32_t N = next_pow2_u32(len);
-    const int k = log2_u32(N);
-    for (int p = 1; p <= k; ++p) {
-        for (int j = p - 1; j >= 0; --j) {
-            for (uint32_t q = threadIdx.x; q < N / 2; q += blockDim.x) {
-                const uint32_t i = ((q >> j) << (j + 1)) | (q & ((1u << j) - 1u));
-                const uint32_t pr = (j == p - 1) ? (i ^ ((2u << j) - 1u)) : (i | (1u << j));
-                if (pr >= len) continue;
-                const K x = a[i], y = a[pr];
-                if (y < x) {
-                    a[i] = y;
-                    a[pr] = x;
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
-// Segments longer than one tile (the large class of a batch), one CTA each,
-// taken from the batch's class-ordered list.  Pairs sort 64-bit composites
-// (key, position) kept in comp at the segment's offset minus comp_base.
-__global__ void __launch_bounds__(kSegThreads)
-k_seg_large(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const int32_t* __restrict__ offs,
-            const int32_t* __restrict__ order, SegPlan* plan, uint64_t* __restrict__ comp, int32_t comp_base)
-{
-    __shared__ int item;
-    const int n_large = plan->hist[kSegClassLarge];
-    const int32_t* list = order + plan->seg_start[kSegClassLarge];
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) item = atomicAdd(&plan->large_counter, 1);
-        __syncthreads();
-        const int i = item;
-        if (i >= n_large) return;
-        const int s = list[i];
-        const int32_t b = offs[s];
-        const uint32_t len = (uint32_t)(offs[s + 1] - b);
-        uint32_t* sk = keys + b;
-        if (!vals) {
-            global_network(sk, len);
-            continue;
-        }
-        uint32_t* sv = vals + b;
-        uint64_t* c = comp + (b - comp_base);
-        for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) c[j] = ((uint64_t)sk[j] << 32) | j;
-        __syncthreads();
-        global_network(c, len);
-        for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) c[j] = (c[j] & ~0xFFFFFFFFull) | sv[(uint32_t)c[j]];
-        __syncthreads();
-        for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) {
-            sk[j] = (uint32_t)(c[j] >> 32);
-            sv[j] = (uint32_t)c[j];
-        }
-    }
-}
 
 // Span of the offsets (first, last) and the longest segment, for planning.
 __global__ void k_seg_stats(const int32_t* __restrict__ offs, int nseg, int* out)
@@ -127,15 +48,6 @@ cudaError_t seg_init_attributes()
 cudaError_t seg_launch_complement(uint32_t* keys, const int32_t* offs, int nseg, int grid, cudaStream_t s)
 {
     k_seg_complement<<<grid, 256, 0, s>>>(keys, offs, nseg);
-    return cudaGetLastError();
-}
-
-cudaError_t seg_launch_large(uint32_t* keys, uint32_t* vals, const int32_t* offs, void* ws, uint64_t* comp,
-                             int32_t comp_base, int grid, cudaStream_t s)
-{
-    SegPlan* plan = reinterpret_cast<SegPlan*>(ws);
-    const int32_t* order = reinterpret_cast<const int32_t*>(plan + 1);
-    k_seg_large<<<grid, kSegThreads, 0, s>>>(keys, vals, offs, order, plan, comp, comp_base);
     return cudaGetLastError();
 }
 

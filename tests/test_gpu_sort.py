@@ -331,6 +331,34 @@ def test_segmented_long_segments(pad_front):
     assert np.array_equal(to_host(tk), wk)
 
 
+@pytest.mark.parametrize("pad_front", [0, 1])
+def test_segmented_pairs_long_segments(pad_front):
+    # Pair segments longer than one 8K-composite tile run the multi-pass plan
+    # of a 2^k composite sort in the persistent launch, with pack, gather and
+    # split passes; many ties, so that equal keys must keep their index order.
+    lens = [3, 1 << 15, 8193, 0, 1 << 17, 100, (1 << 20) + 7, 8192, 40000, 1, (1 << 16) - 1]
+    keys, offs = segments_case(lens, seed=51 + pad_front)
+    keys = (keys >> np.uint32(22)).astype(np.uint32)
+    vals = workloads.uniform_u32(keys.size, seed=52)
+    wk, wv = oracle.segmented_sort_pairs(keys, vals, offs)
+    to = torch.from_numpy(offs).cuda()
+    for _ in range(2):
+        tk, tv = to_dev(keys, pad_front), to_dev(vals, 1 - pad_front)
+        bt.sort_segmented_pairs_(tk, tv, to)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(tk), wk) and np.array_equal(to_host(tv), wv)
+    assert bt.last_device_error() == bt.OK
+    # descending: by key descending, equal keys in ascending index
+    tk, tv = to_dev(keys, pad_front), to_dev(vals, 1 - pad_front)
+    bt.sort_segmented_pairs_(tk, tv, to, ascending=False)
+    dk, dv = keys.copy(), vals.copy()
+    for a, b in zip(offs[:-1], offs[1:]):
+        if b > a:
+            dk[a:b], dv[a:b] = oracle.merge_sort_pairs(keys[a:b], vals[a:b], False)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(tk), dk) and np.array_equal(to_host(tv), dv)
+
+
 def test_segmented_many_long_segments():
     # 300 segments of 16385..70000 keys (a few passes each, many segments per
     # size class) and one of 2^21: the work of every pass interleaves segments
@@ -341,6 +369,14 @@ def test_segmented_many_long_segments():
     bt.sort_segmented_(tk, torch.from_numpy(offs).cuda())
     torch.cuda.synchronize()
     assert np.array_equal(to_host(tk), oracle.segmented_sort(keys, offs))
+    # the same batch as pairs
+    keys = (keys >> np.uint32(20)).astype(np.uint32)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    tk, tv = to_dev(keys), to_dev(vals)
+    bt.sort_segmented_pairs_(tk, tv, torch.from_numpy(offs).cuda())
+    torch.cuda.synchronize()
+    wk, wv = oracle.segmented_sort_pairs(keys, vals, offs)
+    assert np.array_equal(to_host(tk), wk) and np.array_equal(to_host(tv), wv)
 
 
 def test_segmented_batched_workload():
