@@ -629,21 +629,26 @@ def main():
         # the host link alone, just before: one 1 GiB copy each way from and to
         # page-locked memory (best of 3), so that a slow e2e step can be told
         # apart from a slow link
-        link = {"h2d_gbs": 0.0, "d2h_gbs": 0.0}
-        for _ in range(3):
-            for name, dst, src_ in (("h2d_gbs", buf, host_in), ("d2h_gbs", host_out[0], buf)):
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                dst.copy_(src_, non_blocking=True)
-                b.record(stream)
-                torch.cuda.synchronize()
-                link[name] = max(link[name], 4 * n / (a.elapsed_time(b) / 1e3) / 1e9)
+        def measure_link():
+            link = {"h2d_gbs": 0.0, "d2h_gbs": 0.0}
+            for _ in range(3):
+                for name, dst, src_ in (("h2d_gbs", buf, host_in), ("d2h_gbs", host_out[0], buf)):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    dst.copy_(src_, non_blocking=True)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    link[name] = max(link[name], 4 * n / (a.elapsed_time(b) / 1e3) / 1e9)
+            return link
+
+        link = measure_link()
         bt.sort_host_batch([host_in] * 2, host_out)  # warm-up: buffers, streams, plan
         torch.cuda.synchronize()
-        # three timed batch calls, the median reported: the host link of a
-        # shared machine occasionally slows for a while on its own
+        # five timed batch calls, the median reported: the host link of a
+        # shared machine occasionally slows for a while on its own (the link
+        # is measured again after the calls)
         runs = []
-        for _ in range(3):
+        for _ in range(5):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             bt.sort_host_batch([host_in] * args.steps, [host_out[i % 2] for i in range(args.steps)])
@@ -659,10 +664,10 @@ def main():
         torch.cuda.synchronize()
         line["e2e"] = {"value": n / (e2e_ms / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
                        "d2h_bytes_per_step": 4 * n, "ms_per_step": e2e_ms,
-                       "runs_ms_per_step": runs, "timing": "median of 3 batch calls of K steps",
+                       "runs_ms_per_step": runs, "timing": "median of 5 batch calls of K steps",
                        "api": "bitonic_sort_u32_host_batch (one call for the K steps)",
                        "single_call_ms": la.elapsed_time(lb), "single_call_api": "bitonic_sort_u32_host",
-                       "link_gbs": link,
+                       "link_gbs": link, "link_gbs_after": measure_link(),
                        "link_floor_ms": 4 * n / (link["h2d_gbs"] * 1e9) * 1e3 + 4 * n / (link["d2h_gbs"] * 1e9) * 1e3}
         out = host_out[0].numpy().view(np.uint32)
         assert np.all(out[1:] >= out[:-1])
