@@ -482,6 +482,24 @@ def test_typed_keys_large_against_library_sort(kind):
         assert np.array_equal(got.view(ubits), (want if asc else want[::-1]).view(ubits)), (kind, asc)
 
 
+@pytest.mark.parametrize("kind", workloads.TYPED_KEY_KINDS)
+def test_typed_keys_multi_pass_against_oracle(kind):
+    # 2^21 + 5 keys (global passes and a ragged tail) with the special values
+    # mixed in (NaNs of both signs and kinds, signed zeros, infinities,
+    # subnormals, integer extremes), against the typed oracle.  Distinct bit
+    # patterns are distinct in the type's total order, so the descending
+    # result is exactly the ascending one reversed.
+    keys = workloads.typed_keys(kind, (1 << 21) + 5, seed=21, specials=True)
+    want, _ = oracle.bitonic_sort_typed(keys, True)
+    ubits = np.uint64 if keys.dtype.itemsize == 8 else np.uint32
+    for asc in (True, False):
+        t = to_dev_typed(keys)
+        bt.sort_typed_(t, asc, key_type=kind)
+        torch.cuda.synchronize()
+        got = typed_host(t, keys)
+        assert np.array_equal(got.view(ubits), (want if asc else want[::-1]).view(ubits)), (kind, asc)
+
+
 @pytest.mark.parametrize("variant,pipeline", [(1, 0), (2, 0), (0, 1)])
 @pytest.mark.parametrize("kind", ["float32", "int32", "float64", "int64"])
 def test_typed_keys_other_variants(kind, variant, pipeline):
