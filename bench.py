@@ -170,6 +170,46 @@ def segmented_leg(bt, torch, steps, tune_cache=None):
                     "loop with plain launches"}
 
 
+def long_segments_leg(bt, torch, steps):
+    """A batch of segments longer than one tile (64 of 2^15 keys, 16 of 2^17,
+    4 of 2^20: 8.4M keys), which run their own multi-pass plans in one
+    persistent launch: keys only, and as pairs (values = index)."""
+    lens = np.array([1 << 15] * 64 + [1 << 17] * 16 + [1 << 20] * 4, dtype=np.int64)
+    offs_np = np.zeros(lens.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=offs_np[1:])
+    keys_np = workloads.uniform_u32(int(offs_np[-1]), seed=workloads.SEEDS["segmented"] + 1)
+    src = torch.from_numpy(keys_np.view(np.int32)).cuda()
+    buf = src.clone()
+    vals = torch.arange(src.numel(), dtype=torch.int32, device="cuda")
+    vbuf = vals.clone()
+    offs = torch.from_numpy(offs_np.astype(np.int32)).cuda()
+    out = {"segments": int(lens.size), "keys": int(offs_np[-1]),
+           "lengths": "64 x 2^15, 16 x 2^17, 4 x 2^20"}
+    for name, pairs in (("keys", False), ("pairs", True)):
+        def run():
+            if pairs:
+                bt.sort_segmented_pairs_(buf, vbuf, offs)
+            else:
+                bt.sort_segmented_(buf, offs)
+        times = []
+        for i in range(steps + 2):
+            buf.copy_(src)
+            vbuf.copy_(vals)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            run()
+            b.record()
+            torch.cuda.synchronize()
+            if i >= 2:
+                times.append(a.elapsed_time(b))
+        ms = statistics.median(times)
+        got = buf.cpu().numpy().view(np.uint32)
+        ok = all(np.array_equal(got[offs_np[i]:offs_np[i + 1]], np.sort(keys_np[offs_np[i]:offs_np[i + 1]]))
+                 for i in (0, 63, 64, 79, 80, 83))
+        out[name] = {"ms": ms, "gkeys_s": int(offs_np[-1]) / ms / 1e6, "sampled_sorted": bool(ok)}
+    return out
+
+
 def pairs_leg(bt, torch, steps):
     """2^26 key/value pairs, keys uniform over [0, 2^20) (many ties), values =
     original index, ascending, ties by index."""
@@ -679,6 +719,7 @@ def main():
         line["ablation"] = ablation_leg(bt, torch)
     if not args.no_segmented and rank == 0:
         line["segmented"] = segmented_leg(bt, torch, max(3, args.steps), None if args.no_tune else seg_cache)
+        line["segmented"]["long_segments"] = long_segments_leg(bt, torch, max(3, args.steps))
     if not args.no_serving and rank == 0:
         line["serving"] = serving_leg(bt, args.serving_requests)
     if not args.no_cpu_baseline and rank == 0:
