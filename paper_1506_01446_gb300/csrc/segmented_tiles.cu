@@ -112,7 +112,10 @@ k_seg_tiles(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const int3
         const RoundDesc& r0 = P.rounds[0];
         const uint32_t mask = (1u << k) - 1u;
         T tl;
-        // Load in round 0's layout, element by element (segments start anywhere).
+        // Load in round 0's layout, element by element (segments start
+        // anywhere).  A vector's components are consecutive positions of one
+        // segment (every layout vector lies above the vector bits, and k is
+        // at least 3), so its segment is looked up once.
         {
             const uint32_t Lt = thread_local_index<LOG_T>(r0, x);
 #pragma unroll
@@ -121,14 +124,19 @@ k_seg_tiles(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const int3
 #pragma unroll
                 for (int j = 0; j < T::NREG; ++j)
                     if ((v >> j) & 1) Lv ^= r0.reg_loc[j];
+                const int b = (int)(Lv >> k);
+                const uint32_t w0 = Lv & mask;
+                int32_t st = 0, len = 0;
+                if (b < count) {
+                    st = s_start[b];
+                    len = s_len[b];
+                }
 #pragma unroll
                 for (int c = 0; c < T::VEC; ++c) {
-                    const uint32_t L = Lv ^ (uint32_t)c;
-                    const int b = (int)(L >> k);
-                    const uint32_t w = L & mask;
+                    const uint32_t w = w0 + (uint32_t)c;
                     K val = kPad;
-                    if (b < count && (int)w < s_len[b]) {
-                        const uint32_t key = keys[s_start[b] + w];
+                    if ((int)w < len) {
+                        const uint32_t key = keys[st + w];
                         if constexpr (kPairs) val = ((K)key << 32) | w;
                         else val = key;
                     }
@@ -162,14 +170,17 @@ k_seg_tiles(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const int3
 #pragma unroll
                     for (int j = 0; j < T::NREG; ++j)
                         if ((v >> j) & 1) Lv ^= rl.reg_loc[j];
-#pragma unroll
-                    for (int c = 0; c < T::VEC; ++c) {
-                        const uint32_t L = Lv ^ (uint32_t)c;
-                        const int b = (int)(L >> k);
-                        const uint32_t w = L & mask;
-                        if (b < count && (int)w < s_len[b])
-                            gathered[v * T::VEC + c] = vals[s_start[b] + (uint32_t)tl.r[v * T::VEC + c]];
+                    const int b = (int)(Lv >> k);
+                    const uint32_t w0 = Lv & mask;
+                    int32_t st = 0, len = 0;
+                    if (b < count) {
+                        st = s_start[b];
+                        len = s_len[b];
                     }
+#pragma unroll
+                    for (int c = 0; c < T::VEC; ++c)
+                        if ((int)(w0 + (uint32_t)c) < len)
+                            gathered[v * T::VEC + c] = vals[st + (uint32_t)tl.r[v * T::VEC + c]];
                 }
                 __syncthreads();
             }
@@ -179,18 +190,23 @@ k_seg_tiles(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const int3
 #pragma unroll
                 for (int j = 0; j < T::NREG; ++j)
                     if ((v >> j) & 1) Lv ^= rl.reg_loc[j];
+                const int b = (int)(Lv >> k);
+                const uint32_t w0 = Lv & mask;
+                int32_t st = 0, len = 0;
+                if (b < count) {
+                    st = s_start[b];
+                    len = s_len[b];
+                }
 #pragma unroll
                 for (int c = 0; c < T::VEC; ++c) {
-                    const uint32_t L = Lv ^ (uint32_t)c;
-                    const int b = (int)(L >> k);
-                    const uint32_t w = L & mask;
-                    if (b < count && (int)w < s_len[b]) {
+                    const uint32_t w = w0 + (uint32_t)c;
+                    if ((int)w < len) {
                         const K val = tl.r[v * T::VEC + c];
                         if constexpr (kPairs) {
-                            keys[s_start[b] + w] = (uint32_t)(val >> 32);
-                            vals[s_start[b] + w] = gathered[v * T::VEC + c];
+                            keys[st + w] = (uint32_t)(val >> 32);
+                            vals[st + w] = gathered[v * T::VEC + c];
                         } else {
-                            keys[s_start[b] + w] = val;
+                            keys[st + w] = val;
                         }
                     }
                 }
