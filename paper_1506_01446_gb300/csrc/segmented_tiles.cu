@@ -10,6 +10,7 @@
 // whole batch is one asynchronous launch sequence; persistent CTAs take
 // tiles from an atomic counter.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "engine.cuh"
@@ -89,6 +90,8 @@ k_seg_tiles(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const int3
     Vec* sm = reinterpret_cast<Vec*>(smem_raw);
     int32_t* s_start = reinterpret_cast<int32_t*>(smem_raw + (size_t(1) << M) * sizeof(K));
     int32_t* s_len = s_start + kSegMaxPerTile;
+    // the tile's class descriptor, copied from global memory per tile
+    TileParamsBig* s_desc = reinterpret_cast<TileParamsBig*>(s_len + kSegMaxPerTile);
     __shared__ int s_item;
     const uint32_t x = threadIdx.x;
     const int total = plan->total_tiles;
@@ -107,8 +110,15 @@ k_seg_tiles(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const int3
             s_start[b] = offs[s];
             s_len[b] = offs[s + 1] - offs[s];
         }
+        {  // header and rounds of class k's descriptor
+            const TileParamsBig* D = descs + k;
+            const int words = (int)((offsetof(TileParamsBig, rounds) + D->nrounds * sizeof(RoundDesc)) / 4);
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(D);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(s_desc);
+            for (int w = (int)x; w < words; w += (int)blockDim.x) dst[w] = src[w];
+        }
         __syncthreads();
-        const TileParamsBig& P = descs[k];
+        const TileParamsBig& P = *s_desc;
         const RoundDesc& r0 = P.rounds[0];
         const uint32_t mask = (1u << k) - 1u;
         T tl;
@@ -219,7 +229,8 @@ k_seg_tiles(uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, const int3
 template <typename K, int LOG_R, int LOG_T>
 constexpr size_t seg_tile_smem()
 {
-    return (size_t(1) << (LOG_R + LOG_T)) * sizeof(K) + 2 * kSegMaxPerTile * sizeof(int32_t);
+    return (size_t(1) << (LOG_R + LOG_T)) * sizeof(K) + 2 * kSegMaxPerTile * sizeof(int32_t) +
+           sizeof(TileParamsBig);
 }
 
 }  // namespace
