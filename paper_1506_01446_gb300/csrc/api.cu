@@ -572,9 +572,16 @@ cudaError_t launch_plan_tiles(const DeviceState& ds, const PlanEntry& pe, size_t
 // (when that launch works on contiguous tiles; otherwise after it).  Chunk
 // counts are capped at kHostChunks and at the tile count; ev_in / ev_out hold
 // kHostChunks events each.  The caller orders the streams after earlier work.
+// Phases of enqueue_host_sort: the upload, the passes and the download can
+// be enqueued separately (the passes wait on the upload's chunk events, the
+// download on the passes' chunk events), so that a batch can put the next
+// array's upload ahead of this array's download.
+constexpr int kHostUpload = 1, kHostCompute = 2, kHostDownload = 4;
+
 bitonic_status enqueue_host_sort(const DeviceState& ds, const PlanEntry& pe, const uint32_t* in, uint32_t* out,
                                  size_t n, const KeyMaps& km, uint32_t* dev, cudaStream_t up, cudaStream_t comp,
-                                 cudaStream_t down, cudaEvent_t* ev_in, cudaEvent_t* ev_out, int n_up, int n_down)
+                                 cudaStream_t down, cudaEvent_t* ev_in, cudaEvent_t* ev_out, int n_up, int n_down,
+                                 int phases = kHostUpload | kHostCompute | kHostDownload)
 {
     const Plan& pl = pe.plan;
     const size_t L = pl.launches.size();
@@ -591,41 +598,47 @@ bitonic_status enqueue_host_sort(const DeviceState& ds, const PlanEntry& pe, con
     auto keys_of = [&](uint32_t t) { return std::min<size_t>((size_t)t << m, n); };
     const KeyMapHost ident;
     // upload in chunks; the tile sort (launch 0) follows each chunk
-    for (uint32_t c = 0; c < nin; ++c) {
-        const size_t a = keys_of(tiles_of(c, nin)), b = keys_of(tiles_of(c + 1, nin));
-        BT_CK(cudaMemcpyAsync(dev + a, in + a, (b - a) * sizeof(uint32_t), cudaMemcpyHostToDevice, up));
-        BT_CK(cudaEventRecord(ev_in[c], up));
-        BT_CK(cudaStreamWaitEvent(comp, ev_in[c], 0));
-        const bool also_last = L == 1;
-        cudaError_t e = launch_plan_tiles(ds, pe, 0, dev, 0, (uint32_t)n, km.in, also_last ? km.out : ident, comp,
-                                          tiles_of(c, nin), tiles_of(c + 1, nin));
-        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-        if (also_last) BT_CK(cudaEventRecord(ev_out[c], comp));
-    }
-    if (L > 1) {
-        // the middle launches over all tiles, then the last launch
-        for (size_t i = 1; i + 1 < L; ++i) {
-            const Launch& Li = pl.launches[i];
-            const TileParamsBig& D = pl.descs[Li.desc];
-            uint32_t ntiles = Li.grid;
-            if (D.contiguous) ntiles = std::min<uint32_t>(ntiles, (uint32_t)((n + (size_t(1) << D.m) - 1) >> D.m));
-            cudaError_t e = launch_plan_tiles(ds, pe, i, dev, 0, (uint32_t)n, ident, ident, comp, 0, ntiles);
-            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (phases & kHostUpload)
+        for (uint32_t c = 0; c < nin; ++c) {
+            const size_t a = keys_of(tiles_of(c, nin)), b = keys_of(tiles_of(c + 1, nin));
+            BT_CK(cudaMemcpyAsync(dev + a, in + a, (b - a) * sizeof(uint32_t), cudaMemcpyHostToDevice, up));
+            BT_CK(cudaEventRecord(ev_in[c], up));
         }
-        if (last_tiled) {
-            for (uint32_t c = 0; c < nout; ++c) {
-                cudaError_t e = launch_plan_tiles(ds, pe, L - 1, dev, 0, (uint32_t)n, ident, km.out, comp,
-                                                  tiles_of(c, nout), tiles_of(c + 1, nout));
+    if (phases & kHostCompute) {
+        for (uint32_t c = 0; c < nin; ++c) {
+            BT_CK(cudaStreamWaitEvent(comp, ev_in[c], 0));
+            const bool also_last = L == 1;
+            cudaError_t e = launch_plan_tiles(ds, pe, 0, dev, 0, (uint32_t)n, km.in, also_last ? km.out : ident, comp,
+                                              tiles_of(c, nin), tiles_of(c + 1, nin));
+            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+            if (also_last) BT_CK(cudaEventRecord(ev_out[c], comp));
+        }
+        if (L > 1) {
+            // the middle launches over all tiles, then the last launch
+            for (size_t i = 1; i + 1 < L; ++i) {
+                const Launch& Li = pl.launches[i];
+                const TileParamsBig& D = pl.descs[Li.desc];
+                uint32_t ntiles = Li.grid;
+                if (D.contiguous) ntiles = std::min<uint32_t>(ntiles, (uint32_t)((n + (size_t(1) << D.m) - 1) >> D.m));
+                cudaError_t e = launch_plan_tiles(ds, pe, i, dev, 0, (uint32_t)n, ident, ident, comp, 0, ntiles);
                 if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-                BT_CK(cudaEventRecord(ev_out[c], comp));
             }
-        } else {
-            const Launch& Ll = pl.launches[L - 1];
-            cudaError_t e = launch_plan_tiles(ds, pe, L - 1, dev, 0, (uint32_t)n, ident, km.out, comp, 0, Ll.grid);
-            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-            for (uint32_t c = 0; c < nout; ++c) BT_CK(cudaEventRecord(ev_out[c], comp));
+            if (last_tiled) {
+                for (uint32_t c = 0; c < nout; ++c) {
+                    cudaError_t e = launch_plan_tiles(ds, pe, L - 1, dev, 0, (uint32_t)n, ident, km.out, comp,
+                                                      tiles_of(c, nout), tiles_of(c + 1, nout));
+                    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+                    BT_CK(cudaEventRecord(ev_out[c], comp));
+                }
+            } else {
+                const Launch& Ll = pl.launches[L - 1];
+                cudaError_t e = launch_plan_tiles(ds, pe, L - 1, dev, 0, (uint32_t)n, ident, km.out, comp, 0, Ll.grid);
+                if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+                for (uint32_t c = 0; c < nout; ++c) BT_CK(cudaEventRecord(ev_out[c], comp));
+            }
         }
     }
+    if (!(phases & kHostDownload)) return BITONIC_OK;
     // download each chunk once its last launch is done
     for (uint32_t c = 0; c < nout; ++c) {
         const size_t a = keys_of(tiles_of(c, nout)), b = keys_of(tiles_of(c + 1, nout));
@@ -689,12 +702,11 @@ bitonic_status sort_u32_host_impl(const uint32_t* in, uint32_t* out, size_t n, i
                              kHostChunks);
 }
 
-// Batched host-buffer sorts: arrays j = 0..count-1 alternate between two
-// device buffers.  Uploads run on one stream, the passes on a second (one
-// array after another), downloads on a third, so that array j+1's upload
-// and array j-1's download overlap array j's passes.  A buffer is refilled
-// only after its previous download has finished.  Plans that cannot take
-// chunked tile launches run the arrays one after another on `s`.
+// Batched host-buffer sorts: the arrays alternate between two device
+// buffers.  Uploads run on one stream, the passes on a second (one array
+// after another), downloads on a third, so that array j+1's upload and
+// array j-1's download overlap array j's passes.  A buffer is refilled only
+// after its previous download has finished.
 bitonic_status sort_u32_host_batch_impl(const uint32_t* const* in, uint32_t* const* out, const size_t* n, int count,
                                         int ascending, cudaStream_t s)
 {
@@ -748,41 +760,65 @@ bitonic_status sort_u32_host_batch_impl(const uint32_t* const* in, uint32_t* con
         const KeyMaps km = key_maps(KEY_U32, ascending);
         BT_CK(cudaEventRecord(w->bstart, s));
         for (cudaStream_t t : {w->up, w->side, w->down}) BT_CK(cudaStreamWaitEvent(t, w->bstart, 0));
-        for (int j = 0; j < count; ++j) {
-            if (n[j] == 0) continue;
-            const int b = j & 1;
+        // The arrays that hold keys, in order; they alternate between the two
+        // buffers.  Array r+1's upload is enqueued before array r's download,
+        // so that it never waits behind that download in a copy queue (the
+        // download waits for array r's passes): on one in-order copy engine
+        // the other order serialises every step's copies with its passes.
+        std::vector<int> real;
+        for (int j = 0; j < count; ++j)
+            if (n[j]) real.push_back(j);
+        const int R = (int)real.size();
+        std::vector<PlanEntry*> pes(R, nullptr);
+        std::vector<char> tiled(R, 0);
+        for (int r = 0; r < R; ++r) {
+            const int j = real[r];
+            if (n[j] > 1 && (st = get_plan(*ds, n[j], 4, &pes[r]))) return st;
+            PlanEntry* pe = pes[r];
+            tiled[r] = pe && pe->plan.launches[0].kind != KIND_STEP && !pe->opt.pipeline &&
+                       pe->plan.descs[pe->plan.launches[0].desc].contiguous;
+        }
+        // Once the pipeline is full an array's upload ends long before its
+        // passes start and its download overlaps the next array's passes:
+        // only the first upload and the last download are chunked (a chunked
+        // launch leaves a partial wave per chunk).
+        auto phase = [&](int r, int what) -> bitonic_status {
+            const int j = real[r], b = r & 1;
             uint32_t* dev = bufs[b];
             cudaEvent_t* ev_in = w->bev[b];
             cudaEvent_t* ev_out = w->bev[b] + kHostChunks;
             cudaEvent_t ev_free = w->bev[b][2 * kHostChunks];
-            if (j >= 2) BT_CK(cudaStreamWaitEvent(w->up, ev_free, 0));  // buffer b's last download is done
             const size_t bytes = n[j] * sizeof(uint32_t);
-            PlanEntry* pe = nullptr;
-            if (n[j] > 1 && (st = get_plan(*ds, n[j], 4, &pe))) return st;
-            const bool tiles = pe && pe->plan.launches[0].kind != KIND_STEP && !pe->opt.pipeline &&
-                               pe->plan.descs[pe->plan.launches[0].desc].contiguous;
-            if (tiles) {
-                // Once the pipeline is full an array's upload ends long before its
-                // passes start and its download overlaps the next array's
-                // passes: only the first upload and the last download are
-                // chunked (a chunked launch leaves a partial wave per chunk).
-                const int n_up = j == 0 ? kHostChunks : 1, n_down = j + 1 == count ? kHostChunks : 1;
-                if ((st = enqueue_host_sort(*ds, *pe, in[j], out[j], n[j], km, dev, w->up, w->side, w->down, ev_in,
-                                            ev_out, n_up, n_down)))
-                    return st;
-            } else {
-                // upload, sort and download in turn, ordered through the three streams
+            if (what == kHostUpload && r >= 2)
+                BT_CK(cudaStreamWaitEvent(w->up, ev_free, 0));  // buffer b's last download is done
+            if (tiled[r]) {
+                const int n_up = r == 0 ? kHostChunks : 1, n_down = r + 1 == R ? kHostChunks : 1;
+                bitonic_status q = enqueue_host_sort(*ds, *pes[r], in[j], out[j], n[j], km, dev, w->up, w->side,
+                                                     w->down, ev_in, ev_out, n_up, n_down, what);
+                if (q) return q;
+            } else if (what == kHostUpload) {
                 BT_CK(cudaMemcpyAsync(dev, in[j], bytes, cudaMemcpyHostToDevice, w->up));
                 BT_CK(cudaEventRecord(ev_in[0], w->up));
+            } else if (what == kHostCompute) {
                 BT_CK(cudaStreamWaitEvent(w->side, ev_in[0], 0));
-                if (pe && (st = enqueue_plan(*ds, *pe, dev, 0, (uint32_t)n[j], km, 4, ds->status, w->side, nullptr,
-                                             nullptr)))
-                    return st;
+                if (pes[r]) {
+                    bitonic_status q = enqueue_plan(*ds, *pes[r], dev, 0, (uint32_t)n[j], km, 4, ds->status,
+                                                    w->side, nullptr, nullptr);
+                    if (q) return q;
+                }
                 BT_CK(cudaEventRecord(ev_out[0], w->side));
+            } else {
                 BT_CK(cudaStreamWaitEvent(w->down, ev_out[0], 0));
                 BT_CK(cudaMemcpyAsync(out[j], dev, bytes, cudaMemcpyDeviceToHost, w->down));
             }
-            BT_CK(cudaEventRecord(ev_free, w->down));
+            if (what == kHostDownload) BT_CK(cudaEventRecord(ev_free, w->down));
+            return BITONIC_OK;
+        };
+        if (R > 0 && (st = phase(0, kHostUpload))) return st;
+        for (int r = 0; r < R; ++r) {
+            if ((st = phase(r, kHostCompute))) return st;
+            if (r + 1 < R && (st = phase(r + 1, kHostUpload))) return st;
+            if ((st = phase(r, kHostDownload))) return st;
         }
         // the caller's stream continues once every download (hence every pass) is done
         BT_CK(cudaEventRecord(w->bstart, w->down));
