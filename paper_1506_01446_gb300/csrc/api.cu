@@ -1279,7 +1279,7 @@ bitonic_status bitonic_plan_info(size_t n, int pairs, int* launches, int* hbm_pa
     }
     Plan p = make_plan(n, pairs ? 8 : 4, o);
     if (!p.ok) return BITONIC_ERR_UNSUPPORTED;
-    if (launches) *launches = (int)p.launches.size() + (pairs ? (pairs_fused(p, o) ? 1 : 3) : 0);
+    if (launches) *launches = (int)p.launches.size() + (pairs ? (pairs_fused(p, o) ? gather_launches((uint32_t)n) : 3) : 0);
     if (hbm_passes) *hbm_passes = p.hbm_passes;
     if (fused_steps) *fused_steps = p.fused_steps;
     if (global_steps) *global_steps = p.global_steps;

@@ -45,20 +45,41 @@ static __constant__ uint32_t c_ce_mul[2] = {1u, 0xFFFFFFFFu};
 #define BITONIC_CE_FMA_THIRDS 2
 #endif
 
+// Of every three 8-byte compare-exchanges, how many take each 32-bit half
+// of the larger key as a + b - min(a, b) with two multiply-adds (the
+// halves are independent: the minimum is one of the two keys, so each half
+// of it is that key's half).  The others use a ^ b ^ min(a, b).  With all
+// three, the compare and the selects of the minimum (integer ALU) and the
+// four multiply-adds (FMA pipe) split a compare-exchange evenly between the
+// two pipes: 6.81 ms against 7.13 ms (none) and 6.86 ms (two of three) for
+// 2^26 uint64 keys.
+#ifndef BITONIC_CE64_FMA_THIRDS
+#define BITONIC_CE64_FMA_THIRDS 3
+#endif
+
 // Compare-exchange: the lower register receives the key that sorts first.
-// fma_hi: the multiply-add form (4-byte keys; exact modulo 2^32, since the
-// minimum is one of the two keys).  Constant once the caller's loop unrolls.
-// 8-byte keys take the larger key as a ^ b ^ min(a, b): one 64-bit compare
-// and two selects, then two logic ops instead of two more selects (9.0 vs
-// 6.9 compare-exchanges per clock per SM in a register-only probe).
+// third: the compare-exchange's position modulo 3 within its step, which
+// picks its form (constant once the caller's loop unrolls).  4-byte keys:
+// the multiply-add form (exact modulo 2^32, since the minimum is one of the
+// two keys) or a min and a max.  8-byte keys: one 64-bit compare and two
+// selects for the minimum, then the larger key from multiply-adds or from
+// logic ops (the latter 9.0 vs 6.9 compare-exchanges per clock per SM
+// against two more selects in a register-only probe).
 template <bool DESC, typename K>
-__device__ __forceinline__ void cmpx(K& a, K& b, bool fma_hi = false)
+__device__ __forceinline__ void cmpx(K& a, K& b, int third = 3)
 {
     K lo, hi;
-    if (sizeof(K) == 4 && fma_hi) {
+    if (sizeof(K) == 4 && third < BITONIC_CE_FMA_THIRDS) {
         lo = a < b ? a : b;
         const K sum = a * c_ce_mul[0] + b;
         hi = lo * c_ce_mul[1] + sum;
+    } else if (sizeof(K) == 8 && third < BITONIC_CE64_FMA_THIRDS) {
+        lo = a < b ? a : b;
+        const uint32_t s0 = (uint32_t)a * c_ce_mul[0] + (uint32_t)b;
+        const uint32_t s1 = (uint32_t)(a >> 32) * c_ce_mul[0] + (uint32_t)(b >> 32);
+        const uint32_t h0 = (uint32_t)lo * c_ce_mul[1] + s0;
+        const uint32_t h1 = (uint32_t)(lo >> 32) * c_ce_mul[1] + s1;
+        hi = ((K)h1 << 32) | h0;
     } else if (sizeof(K) == 8) {
         lo = a < b ? a : b;
         hi = a ^ b ^ lo;
@@ -79,7 +100,7 @@ __device__ __forceinline__ void net_step(K (&r)[R])
     for (int i = 0; i < R; ++i) {
         if (i & (1 << Q)) continue;
         const int j = FLIP ? (i ^ ((2 << Q) - 1)) : (i | (1 << Q));
-        cmpx<DESC>(r[i], r[j], ((i + Q) % 3) < BITONIC_CE_FMA_THIRDS);
+        cmpx<DESC>(r[i], r[j], (i + Q) % 3);
     }
 }
 

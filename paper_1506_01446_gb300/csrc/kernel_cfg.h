@@ -98,8 +98,11 @@ bool tile_pairs_supported(int cfg);
 cudaError_t launch_tile_pairs(int cfg, int mode, uint64_t* comp, uint32_t hi, const TileParams* hP, uint32_t grid,
                               const PairIo& pio, uint32_t pf_dist, cudaStream_t s);
 cudaError_t init_tile_pairs_attributes();
-// out[i] = vals[idx[i]] for i < n (out and idx 16-byte aligned).
+// out[i] = vals[idx[i]] for i < n (out and idx 16-byte aligned), in
+// gather_launches(n) launches: above a size the sources are taken in slices
+// that fit L2, one launch per slice.
 cudaError_t launch_gather_by_index(uint32_t* out, const uint32_t* vals, const uint32_t* idx, uint32_t n,
                                    cudaStream_t s);
+int gather_launches(uint32_t n);
 
 }  // namespace bitonic
