@@ -229,6 +229,22 @@ def test_pairs_n26_ties_by_index():
     assert np.array_equal(gk, wk) and np.array_equal(gv, wv)
 
 
+
+@pytest.mark.parametrize("n, kf, vf, ascending", [((1 << 24) + 5, 0, 0, True), (3 * (1 << 23) + 3, 1, 2, False)])
+def test_pairs_sliced_gather_ragged(n, kf, vf, ascending):
+    # Above 2^24 pairs the values are gathered in slices of at most 2^24
+    # sources, one launch per slice (two here), each launch's ragged tail
+    # handled element by element; keys and values off 16-byte boundaries in
+    # the second case.
+    keys = (workloads.uniform_u32(n, seed=n + 11) >> np.uint32(12)).astype(np.uint32)
+    vals = workloads.uniform_u32(n, seed=n + 13)
+    wk, wv = oracle.merge_sort_pairs(keys, vals, ascending)
+    tk, tv = to_dev(keys, kf), to_dev(vals, vf)
+    bt.sort_pairs_(tk, tv, ascending)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(tk), wk) and np.array_equal(to_host(tv), wv)
+    assert bt.plan_info(n, pairs=True)["launches"] == bt.plan_info(n, pairs=True)["hbm_passes"] + 2
+
 def segments_case(lens, seed, gap_every=0):
     lens = np.asarray(lens, dtype=np.int64)
     offs = np.zeros(lens.size + 1, dtype=np.int64)
