@@ -312,19 +312,23 @@ def serving_leg(bt, requests):
                workload the latency target is quoted at);
       batched_20k / batched_50k: 20,000 and 50,000 req/s, sizes log-uniform
                in [2^10, 2^14] keys, where requests overlap and the loop
-               packs many into each launch."""
+               packs many into each launch.
+    The loop is the library's (bitonic_serve_run); batched_50k_python_loop
+    repeats the 50,000 req/s point with the same loop written in Python."""
     from paper_1506_01446_gb300.serving import SortServer
     pool = workloads.uniform_u32(1 << 26, seed=7)
     pool_v = np.arange(1 << 26, dtype=np.uint32)
     srv = SortServer(pool, pool_v, budget_bytes=16 << 30, streams=4)
     out = {}
-    for name, rate, hi_log2 in (("stated", 2000.0, 22), ("batched_20k", 20000.0, 14), ("batched_50k", 50000.0, 14)):
+    for name, rate, hi_log2, engine in (("stated", 2000.0, 22, "native"), ("batched_20k", 20000.0, 14, "native"),
+                                        ("batched_50k", 50000.0, 14, "native"),
+                                        ("batched_50k_python_loop", 50000.0, 14, "python")):
         arr, sizes, hv = workloads.serving_requests(requests, seed=workloads.SEEDS["serving"], rate=rate,
                                                     hi_log2=hi_log2)
         srv.warmup(int(sizes.max()))                     # workspaces and plans before the clock starts
         warm = min(200, requests)
-        srv.run(arr[:warm], sizes[:warm], hv[:warm])
-        stats = srv.run(arr, sizes, hv)
+        srv.run(arr[:warm], sizes[:warm], hv[:warm], engine=engine)
+        stats = srv.run(arr, sizes, hv, engine=engine)
         stats["rate_req_s"] = rate
         stats["sizes"] = f"log-uniform [2^10, 2^{hi_log2}] keys, 30% with values"
         out[name] = stats

@@ -394,6 +394,82 @@ size_t bitonic_debug_desc_size(void);
 bitonic_status bitonic_sort_pairs_u32_noalloc(uint32_t *keys, uint32_t *vals, size_t n, int ascending,
                                               bitonic_stream_t stream);
 
+/*
+ * Continuous-batching sort server (no paper counterpart; a deployment loop
+ * around the sorts above).  bitonic_serve_run serves a whole stream of
+ * requests on the calling host thread and returns when every request is
+ * done:
+ *   - Requests (reqs[0..nreq), arrival_s non-decreasing, seconds after the
+ *     call's start) become pending when the host clock reaches their
+ *     arrival.  Pending requests are admitted in arrival order while their
+ *     device buffers fit cfg->dev_arena and their results fit the host
+ *     output area (first fit in 16-byte units; a request that does not fit
+ *     stops admission until a completion frees space).
+ *   - Small requests (n <= small_keys keys-only, n <= small_pairs key/value)
+ *     admitted in one pass are packed, at most max_batch per launch, into one
+ *     bitonic_sort_segmented_u32 or bitonic_sort_segmented_pairs_u32_bounded
+ *     launch per kind; a larger request gets its own bitonic_sort_u32 or
+ *     bitonic_sort_pairs_u32.  Every request is sorted ascending (pairs: ties
+ *     by index), exactly as sorted alone.
+ *   - Each launch takes the next of cfg->streams in turn: its inputs are
+ *     copied from the host pools, its segment offsets from cfg->offs_stage,
+ *     its results back to out_keys / out_vals, all on that stream; an event
+ *     marks it done, and the loop polls those events between admissions.
+ *   - done_s[i] = the host time (seconds after the start) at which the loop
+ *     saw request i's launch complete; out_pos[i] = the first key of its
+ *     result in out_keys (and out_vals).  With keep_outputs == 0 result
+ *     space is reused once the loop has seen a launch complete, so read
+ *     results only with keep_outputs != 0 (then out_cap must hold every
+ *     request's keys).
+ *   - Graph replay is off for this thread during the call (plain launches;
+ *     the thread's previous mode is restored).  Call the sorts once per
+ *     stream beforehand for the sizes to come if no request should pay for
+ *     workspace allocation or planning.
+ *   - Ownership: every buffer is the caller's; host buffers should be page
+ *     locked (the copies are asynchronous); dev_arena 16-byte aligned.
+ *   - BITONIC_ERR_INVALID for a null or inconsistent argument, a request with
+ *     n == 0, a source range outside the pools, or a request larger than the
+ *     device arena or the output area (it could never be admitted).  A sort
+ *     or CUDA error stops the loop: every stream is synchronised, the status
+ *     is returned, and done_s of unfinished requests is negative.
+ */
+typedef struct {
+    double arrival_s;   /* seconds after the start of the call */
+    uint64_t src;       /* first key (and value) in in_keys / in_vals */
+    uint32_t n;         /* keys, >= 1 */
+    int32_t has_vals;   /* nonzero: a key/value request */
+} bitonic_serve_request;
+
+typedef struct {
+    void *dev_arena;                  /* device memory the buffers are carved from */
+    size_t dev_bytes;                 /* its size: the device memory budget */
+    const uint32_t *in_keys;          /* input pools, pool_len entries each (host) */
+    const uint32_t *in_vals;          /* may be NULL when no request has values */
+    size_t pool_len;
+    uint32_t *out_keys;               /* result area, out_cap entries each (host) */
+    uint32_t *out_vals;               /* may be NULL when no request has values */
+    size_t out_cap;
+    int32_t *offs_stage;              /* staging for segment offsets, offs_cap entries (host) */
+    size_t offs_cap;
+    const bitonic_stream_t *streams;  /* launches go to these in turn */
+    int nstreams;
+    uint32_t small_keys;              /* packed keys-only requests: n <= small_keys (<= 16384) */
+    uint32_t small_pairs;             /* packed key/value requests: n <= small_pairs (<= 8192) */
+    int max_batch;                    /* most requests per packed launch (>= 1) */
+    int keep_outputs;                 /* nonzero: result space is never reused */
+} bitonic_serve_config;
+
+typedef struct {
+    double span_s;              /* first arrival to last completion */
+    int64_t batches;            /* packed launches */
+    int64_t batched_requests;   /* requests in packed launches */
+    int64_t large_launches;     /* requests sorted alone */
+    uint64_t peak_device_bytes; /* most of dev_arena in use at once */
+} bitonic_serve_stats;
+
+bitonic_status bitonic_serve_run(const bitonic_serve_config *cfg, const bitonic_serve_request *reqs, int nreq,
+                                 double *done_s, uint64_t *out_pos, bitonic_serve_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,7 @@ EXPORTS = (
     "bitonic_set_class_options", "bitonic_sort_i32", "bitonic_sort_f32", "bitonic_sort_u64", "bitonic_sort_i64",
     "bitonic_sort_f64", "bitonic_sort_u32_host", "bitonic_sort_u32_host_batch",
     "bitonic_sort_segmented_u32_dir", "bitonic_sort_segmented_pairs_u32_dir", "bitonic_set_thread_graphs",
-    "bitonic_debug_set_wait", "bitonic_set_segmented_options",
+    "bitonic_debug_set_wait", "bitonic_set_segmented_options", "bitonic_serve_run",
 )
 
 # torch dtype name -> C entry point of the keys-only sorts (uint64 keys may be
@@ -57,6 +57,29 @@ class Options(ctypes.Structure):
 
 class SegOptions(ctypes.Structure):
     _fields_ = [("tile_log2", ctypes.c_int), ("class_floor_gap", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+
+class ServeConfig(ctypes.Structure):
+    """bitonic_serve_config (include/bitonic.h)."""
+    _fields_ = [("dev_arena", ctypes.c_void_p), ("dev_bytes", ctypes.c_size_t),
+                ("in_keys", ctypes.c_void_p), ("in_vals", ctypes.c_void_p), ("pool_len", ctypes.c_size_t),
+                ("out_keys", ctypes.c_void_p), ("out_vals", ctypes.c_void_p), ("out_cap", ctypes.c_size_t),
+                ("offs_stage", ctypes.c_void_p), ("offs_cap", ctypes.c_size_t),
+                ("streams", ctypes.POINTER(ctypes.c_void_p)), ("nstreams", ctypes.c_int),
+                ("small_keys", ctypes.c_uint32), ("small_pairs", ctypes.c_uint32), ("max_batch", ctypes.c_int),
+                ("keep_outputs", ctypes.c_int)]
+
+
+class ServeStats(ctypes.Structure):
+    """bitonic_serve_stats (include/bitonic.h)."""
+    _fields_ = [("span_s", ctypes.c_double), ("batches", ctypes.c_int64), ("batched_requests", ctypes.c_int64),
+                ("large_launches", ctypes.c_int64), ("peak_device_bytes", ctypes.c_uint64)]
+
+
+def serve_request_dtype():
+    """numpy layout of bitonic_serve_request."""
+    import numpy as np
+    return np.dtype([("arrival_s", "<f8"), ("src", "<u8"), ("n", "<u4"), ("has_vals", "<i4")])
 
 
 _lib = None
@@ -103,6 +126,7 @@ def load() -> ctypes.CDLL:
     lib.bitonic_set_thread_graphs.argtypes = [i32]
     lib.bitonic_debug_set_wait.argtypes = [i32, ctypes.c_uint]
     lib.bitonic_set_segmented_options.argtypes = [i32, i32, ctypes.POINTER(SegOptions)]
+    lib.bitonic_serve_run.argtypes = [ctypes.POINTER(ServeConfig), vp, i32, vp, vp, ctypes.POINTER(ServeStats)]
     for name in EXPORTS:
         f = getattr(lib, name)
         if f.restype is ctypes.c_int or f.restype is None:

@@ -22,7 +22,7 @@ LIB = os.path.join(OUT_DIR, "libbitonic.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["api.cu", "plan.cpp", "kernels.cu", "tile_u32.cu", "tile_u64.cu", "kernels_pipe.cu", "segmented.cu", "segmented_tiles.cu", "noalloc.cu", "tile_pairs.cu", "seg_long.cu"]
+SOURCES = ["api.cu", "plan.cpp", "kernels.cu", "tile_u32.cu", "tile_u64.cu", "kernels_pipe.cu", "segmented.cu", "segmented_tiles.cu", "noalloc.cu", "tile_pairs.cu", "seg_long.cu", "serve.cpp"]
 
 
 def _nvcc() -> str:

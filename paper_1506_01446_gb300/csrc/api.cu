@@ -986,6 +986,14 @@ bitonic_status sort_segmented_dir_impl(uint32_t* keys, uint32_t* vals, const int
 
 }  // namespace
 
+int thread_graph_mode() { return t_graph_mode; }
+
+bitonic_status report_error(bitonic_status st, const std::string& what)
+{
+    t_last_error = what;
+    return st;
+}
+
 }  // namespace bitonic
 
 using namespace bitonic;

@@ -4,8 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
+#include "bitonic.h"
 #include "desc.h"
 
 namespace bitonic {
@@ -79,5 +81,11 @@ cudaError_t launch_pairs_unpack(const uint64_t* comp, uint32_t* keys, uint32_t* 
                                 int desc, cudaStream_t s);
 
 cudaError_t init_tile_attributes();
+
+// Graph replay mode of the calling host thread (bitonic_set_thread_graphs).
+int thread_graph_mode();
+
+// Sets the calling thread's last error message; returns st.
+bitonic_status report_error(bitonic_status st, const std::string& what);
 
 }  // namespace bitonic

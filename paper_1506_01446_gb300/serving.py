@@ -17,16 +17,22 @@ Requests (uint32 keys, some with uint32 values) arrive over time.  The loop:
     the request's buffers and timestamping it on the host monotonic clock.
 
 Latency = completion - arrival, including queueing.  The sorts themselves are
-the library's CUDA kernels; this module only schedules them.
+the library's CUDA kernels.  By default the loop runs inside the library
+(bitonic_serve_run: one C++ host thread, plain CUDA runtime calls per copy
+and launch); this module sets up the buffers and streams, warms the plans up
+and computes the statistics.  The same loop written in Python
+(engine="python") is kept for comparison: at high request rates its
+per-call overhead, not the GPU, sets the latency.
 """
 from __future__ import annotations
 
+import ctypes
 import time
 from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import load, OK, status_string, thread_graphs
+from . import load, OK, status_string, thread_graphs, ServeConfig, ServeStats, serve_request_dtype
 
 ALIGN = 16
 
@@ -266,15 +272,83 @@ class SortServer:
             torch.cuda.synchronize()
 
     # -- the loop --------------------------------------------------------------
-    def run(self, arrival_s, sizes, has_vals, keep_outputs: bool = False):
+    def run(self, arrival_s, sizes, has_vals, keep_outputs: bool = False, engine: str = "native"):
         """Serves the request stream; returns a statistics dict (and, with
-        keep_outputs, the sorted keys / values of every request)."""
-        torch = self.torch
-        self._rr = 0
+        keep_outputs, the sorted keys / values of every request).
+
+        engine "native": the loop runs in the library (bitonic_serve_run, one
+        C++ host thread); "python": the same loop written here, one ctypes and
+        torch call per copy and launch."""
         reqs = []
         for i, (a, n, hv) in enumerate(zip(arrival_s, sizes, has_vals)):
             kind = self._kind(int(n), bool(hv))
             reqs.append(Request(i, float(a), int(n), bool(hv), self._src(kind, int(n))))
+        if engine == "native":
+            return self._run_native(reqs, keep_outputs)
+        if engine != "python":
+            raise ValueError(f"unknown engine {engine!r}")
+        return self._run_python(reqs, keep_outputs)
+
+    def _stats(self, reqs, batch_sizes_sum, n_batches, n_large, peak, engine):
+        lat = np.array([r.done - r.arrival for r in reqs])
+        keys_total = int(sum(r.n for r in reqs))
+        span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+        return {
+            "requests": len(reqs), "keys": keys_total,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
+            "sustained_gkeys_s": keys_total / span / 1e9,
+            "offered_gkeys_s": keys_total / max(reqs[-1].arrival, 1e-9) / 1e9,
+            "batches": n_batches, "mean_batch": batch_sizes_sum / n_batches if n_batches else 0.0,
+            "large_launches": n_large, "peak_device_bytes": peak, "budget_bytes": self.budget,
+            "streams": len(self.streams), "engine": engine,
+        }
+
+    def _run_native(self, reqs, keep_outputs):
+        torch = self.torch
+        N = len(reqs)
+        rq = np.zeros(N, dtype=serve_request_dtype())
+        rq["arrival_s"] = [r.arrival for r in reqs]
+        rq["src"] = [r.src for r in reqs]
+        rq["n"] = [r.n for r in reqs]
+        rq["has_vals"] = [int(r.has_vals) for r in reqs]
+        if keep_outputs:
+            # every result keeps its own place: one area for the whole stream
+            total = int(sum((r.n + 3) // 4 * 4 for r in reqs))
+            out_k = torch.empty(total, dtype=torch.int32).pin_memory()
+            out_v = torch.empty(total, dtype=torch.int32).pin_memory()
+        else:
+            out_k, out_v = self.out_keys, self.out_vals
+        handles = (ctypes.c_void_p * len(self.streams))(*[st.cuda_stream for st in self.streams])
+        cfg = ServeConfig(dev_arena=self.dev_base, dev_bytes=self.budget,
+                          in_keys=self.in_keys.data_ptr(), in_vals=self.in_vals.data_ptr(),
+                          pool_len=self.in_keys.numel(), out_keys=out_k.data_ptr(), out_vals=out_v.data_ptr(),
+                          out_cap=out_k.numel(), offs_stage=self.offs_stage.data_ptr(),
+                          offs_cap=self.offs_stage.numel(), streams=handles, nstreams=len(self.streams),
+                          small_keys=self.small_keys, small_pairs=self.small_pairs, max_batch=self.max_batch,
+                          keep_outputs=int(bool(keep_outputs)))
+        done = np.zeros(N, dtype=np.float64)
+        pos = np.zeros(N, dtype=np.uint64)
+        st = ServeStats()
+        torch.cuda.synchronize()
+        status = self.lib.bitonic_serve_run(ctypes.byref(cfg), rq.ctypes.data, N, done.ctypes.data,
+                                            pos.ctypes.data, ctypes.byref(st))
+        if status != OK:
+            raise RuntimeError(f"bitonic_serve_run failed: {status_string(status)}")
+        for r, d, p in zip(reqs, done, pos):
+            r.done, r.out = float(d), int(p)
+        stats = self._stats(reqs, st.batched_requests, st.batches, st.large_launches, st.peak_device_bytes,
+                            "native")
+        if not keep_outputs:
+            return stats
+        ok, ov = out_k.numpy().view(np.uint32), out_v.numpy().view(np.uint32)
+        outputs = [(ok[r.out:r.out + r.n].copy(), ov[r.out:r.out + r.n].copy() if r.has_vals else None)
+                   for r in reqs]
+        return stats, outputs
+
+    def _run_python(self, reqs, keep_outputs):
+        torch = self.torch
+        self._rr = 0
         N = len(reqs)
         outputs = [None] * N if keep_outputs else None
         pending, inflight = [], []
@@ -361,17 +435,5 @@ class SortServer:
                     wait = reqs[nxt].arrival - (time.perf_counter() - t0)
                     if wait > 2e-4:
                         time.sleep(wait - 1e-4)
-        lat = np.array([r.done - r.arrival for r in reqs])
-        keys_total = int(sum(r.n for r in reqs))
-        span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
-        stats = {
-            "requests": N, "keys": keys_total,
-            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
-            "sustained_gkeys_s": keys_total / span / 1e9,
-            "offered_gkeys_s": keys_total / max(reqs[-1].arrival, 1e-9) / 1e9,
-            "batches": n_batches, "mean_batch": float(np.mean(batch_sizes)) if batch_sizes else 0.0,
-            "large_launches": n_large, "peak_device_bytes": self.arena.peak, "budget_bytes": self.budget,
-            "streams": len(self.streams),
-        }
+        stats = self._stats(reqs, float(sum(batch_sizes)), n_batches, n_large, self.arena.peak, "python")
         return (stats, outputs) if keep_outputs else stats

@@ -102,3 +102,42 @@ def test_debug_wait_argument_check_needs_no_gpu():
     # a starving test mode needs a bound of at least one try (checked before
     # any device work)
     assert bt.load().bitonic_debug_set_wait(1, 0) == bt.ERR_INVALID
+
+
+def test_serve_run_rejects_bad_arguments_before_any_cuda_call():
+    import numpy as np
+    lib = bt.load()
+    dt = bt.serve_request_dtype()
+    assert dt.itemsize == 24
+    stats = bt.ServeStats()
+    done = np.zeros(4, dtype=np.float64)
+    pos = np.zeros(4, dtype=np.uint64)
+    streams = (ctypes.c_void_p * 1)(None)
+
+    def cfg(**kw):
+        base = dict(dev_arena=4096, dev_bytes=1 << 20, in_keys=4096, in_vals=4096, pool_len=1 << 16,
+                    out_keys=4096, out_vals=4096, out_cap=1 << 16, offs_stage=4096, offs_cap=1024,
+                    streams=streams, nstreams=1, small_keys=16384, small_pairs=8192, max_batch=64, keep_outputs=0)
+        base.update(kw)
+        return bt.ServeConfig(**base)
+
+    def run(c, reqs):
+        r = np.zeros(len(reqs), dtype=dt)
+        for i, (a, src, n, hv) in enumerate(reqs):
+            r[i] = (a, src, n, hv)
+        return lib.bitonic_serve_run(ctypes.byref(c) if c is not None else None, r.ctypes.data, len(reqs),
+                                     done.ctypes.data, pos.ctypes.data, ctypes.byref(stats))
+
+    assert run(None, []) == bt.ERR_INVALID
+    assert run(cfg(), []) == bt.OK                                            # nothing to serve
+    assert run(cfg(dev_arena=4100), [(0.0, 0, 10, 0)]) == bt.ERR_INVALID      # arena not 16-byte aligned
+    assert run(cfg(nstreams=0), [(0.0, 0, 10, 0)]) == bt.ERR_INVALID
+    assert run(cfg(small_keys=1 << 15), [(0.0, 0, 10, 0)]) == bt.ERR_INVALID  # beyond one packed tile
+    assert run(cfg(), [(0.0, 0, 0, 0)]) == bt.ERR_INVALID                     # empty request
+    assert run(cfg(), [(0.0, (1 << 16) - 5, 10, 0)]) == bt.ERR_INVALID        # source beyond the pool
+    assert run(cfg(), [(1.0, 0, 10, 0), (0.5, 0, 10, 0)]) == bt.ERR_INVALID   # arrivals out of order
+    assert run(cfg(in_vals=None), [(0.0, 0, 10, 1)]) == bt.ERR_INVALID        # values without a pool
+    assert run(cfg(dev_bytes=1 << 12), [(0.0, 0, 5000, 0)]) == bt.ERR_INVALID  # never fits the arena
+    assert run(cfg(out_cap=100), [(0.0, 0, 200, 0)]) == bt.ERR_INVALID        # never fits the output area
+    assert run(cfg(keep_outputs=1, out_cap=300), [(0.0, 0, 200, 0), (0.0, 200, 200, 0)]) == bt.ERR_INVALID
+    assert "keep_outputs" in bt.last_error_message()

@@ -25,7 +25,7 @@ def test_arena_first_fit_and_coalescing():
     assert a.alloc(2 << 20) is None                         # larger than the budget
 
 
-def _serve(n_req, seed, budget, hi_log2, rate=2000.0):
+def _serve(n_req, seed, budget, hi_log2, rate=2000.0, engine="native"):
     torch = pytest.importorskip("torch")
     from paper_1506_01446_gb300.serving import SortServer
     arr, sizes, hv = workloads.serving_requests(n_req, seed=seed, rate=rate, lo_log2=10, hi_log2=hi_log2)
@@ -34,15 +34,16 @@ def _serve(n_req, seed, budget, hi_log2, rate=2000.0):
     srv = SortServer(pool, pool_v, budget_bytes=budget, streams=4)
     if budget >= 1 << 30:
         srv.warmup(int(sizes.max()))
-    stats, outs = srv.run(arr, sizes, hv, keep_outputs=True)
+    stats, outs = srv.run(arr, sizes, hv, keep_outputs=True, engine=engine)
     reqs = [(srv._kind(int(n), bool(h)), int(n), bool(h)) for n, h in zip(sizes, hv)]
     return srv, stats, outs, reqs, pool, pool_v, torch
 
 
 @pytest.mark.gpu
-def test_mixed_stream_results_match_oracle_and_alone():
+@pytest.mark.parametrize("engine", ["native", "python"])
+def test_mixed_stream_results_match_oracle_and_alone(engine):
     import paper_1506_01446_gb300 as bt
-    srv, stats, outs, reqs, pool, pool_v, torch = _serve(300, 5, 1 << 30, hi_log2=17)
+    srv, stats, outs, reqs, pool, pool_v, torch = _serve(300, 5, 1 << 30, hi_log2=17, engine=engine)
     assert stats["requests"] == 300 and stats["batches"] > 0
     # re-derive each request's input slice the way the server assigned it
     probe = type(srv).__new__(type(srv))
@@ -67,8 +68,9 @@ def test_mixed_stream_results_match_oracle_and_alone():
 
 
 @pytest.mark.gpu
-def test_tiny_budget_still_serves_everything():
-    srv, stats, outs, reqs, pool, pool_v, torch = _serve(80, 9, 6 << 20, hi_log2=18)
+@pytest.mark.parametrize("engine", ["native", "python"])
+def test_tiny_budget_still_serves_everything(engine):
+    srv, stats, outs, reqs, pool, pool_v, torch = _serve(80, 9, 6 << 20, hi_log2=18, engine=engine)
     assert stats["peak_device_bytes"] <= 6 << 20
     assert all(o is not None for o in outs)
     for (k, v), (_, n, has_v) in zip(outs, reqs):
@@ -76,13 +78,14 @@ def test_tiny_budget_still_serves_everything():
 
 
 @pytest.mark.gpu
-def test_batched_stream_packs_many_requests_and_matches_oracle():
+@pytest.mark.parametrize("engine", ["native", "python"])
+def test_batched_stream_packs_many_requests_and_matches_oracle(engine):
     # A stream fast enough that requests overlap (200,000 req/s, sizes up to
     # 2^14 keys): the loop packs many requests into each segmented launch,
     # and every result is still exactly the oracle's and the same as the
     # request sorted alone.
     import paper_1506_01446_gb300 as bt
-    srv, stats, outs, reqs, pool, pool_v, torch = _serve(600, 7, 1 << 30, hi_log2=14, rate=200000.0)
+    srv, stats, outs, reqs, pool, pool_v, torch = _serve(600, 7, 1 << 30, hi_log2=14, rate=200000.0, engine=engine)
     assert stats["mean_batch"] > 4, stats
     probe = type(srv).__new__(type(srv))
     probe.rings, probe.ring_pos = srv.rings, {k: 0 for k in srv.rings}
@@ -107,10 +110,11 @@ def test_batched_stream_packs_many_requests_and_matches_oracle():
 
 
 @pytest.mark.gpu
-def test_server_leaves_other_threads_graph_mode_alone():
+@pytest.mark.parametrize("engine", ["native", "python"])
+def test_server_leaves_other_threads_graph_mode_alone(engine):
     # The server turns graph replay off for its own thread only: the
     # process-wide option is unchanged during and after a run.
     import paper_1506_01446_gb300 as bt
     before = bt.get_options()["use_graph"]
-    _serve(40, 11, 1 << 28, hi_log2=15)
+    _serve(40, 11, 1 << 28, hi_log2=15, engine=engine)
     assert bt.get_options()["use_graph"] == before
