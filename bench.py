@@ -310,9 +310,9 @@ def serving_leg(bt, requests):
     with values, 16 GiB device budget, continuous batching:
       stated:  2,000 req/s, sizes log-uniform in [2^10, 2^22] keys (the
                workload the latency target is quoted at);
-      batched_20k / batched_50k: 20,000 and 50,000 req/s, sizes log-uniform
-               in [2^10, 2^14] keys, where requests overlap and the loop
-               packs many into each launch.
+      batched_20k / batched_50k / batched_200k: 20,000, 50,000 and 200,000
+               req/s, sizes log-uniform in [2^10, 2^14] keys, where requests
+               overlap and the loop packs those that wait into one launch.
     The loop is the library's (bitonic_serve_run); batched_50k_python_loop
     repeats the 50,000 req/s point with the same loop written in Python."""
     from paper_1506_01446_gb300.serving import SortServer
@@ -322,6 +322,7 @@ def serving_leg(bt, requests):
     out = {}
     for name, rate, hi_log2, engine in (("stated", 2000.0, 22, "native"), ("batched_20k", 20000.0, 14, "native"),
                                         ("batched_50k", 50000.0, 14, "native"),
+                                        ("batched_200k", 200000.0, 14, "native"),
                                         ("batched_50k_python_loop", 50000.0, 14, "python")):
         arr, sizes, hv = workloads.serving_requests(requests, seed=workloads.SEEDS["serving"], rate=rate,
                                                     hi_log2=hi_log2)
