@@ -238,6 +238,33 @@ def pairs_leg(bt, torch, steps):
     return {"n": n, "ms": ms, "gpairs_s": n / ms / 1e6, "plan": info, "sampled_sorted": bool(np.all(out_k[1:] >= out_k[:-1]))}
 
 
+def distributions_leg(bt, torch, steps):
+    """The network's compare-exchanges do not depend on the data (Section
+    3.2), so a sort's time should not either: 2^24 uint32 keys of each of
+    the five input distributions, ascending, median of `steps` sorts each
+    (inputs restored by a device copy before each sort)."""
+    n = 1 << 24
+    stream = torch.cuda.current_stream()
+    out = {}
+    for dist in workloads.DISTRIBUTIONS:
+        src = torch.from_numpy(workloads.keys_u32(dist, n, seed=workloads.SEEDS["n24"]).view(np.int32)).cuda()
+        buf = src.clone()
+        for _ in range(3):
+            buf.copy_(src)
+            bt.sort_(buf)
+        times = []
+        for _ in range(steps):
+            buf.copy_(src)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bt.sort_(buf)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        out[dist] = statistics.median(times)
+    return {"n": n, "ms": out, "max_over_min": max(out.values()) / min(out.values())}
+
+
 def key_types_leg(bt, torch, steps, peak_gbs):
     """Keys-only sorts of the other key types, 512 MiB each (inputs larger
     than L2): 2^27 int32 / float32 keys, 2^26 uint64 / int64 / float64 keys,
@@ -722,6 +749,7 @@ def main():
         line["pairs"] = pairs_leg(bt, torch, max(3, args.steps))
     if not args.no_key_types and rank == 0:
         line["key_types"] = key_types_leg(bt, torch, max(3, args.steps), hbm_gbs)
+        line["data_oblivious"] = distributions_leg(bt, torch, max(5, args.steps))
     if not args.no_ablation and rank == 0:
         line["ablation"] = ablation_leg(bt, torch)
     if not args.no_segmented and rank == 0:
