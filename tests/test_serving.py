@@ -118,3 +118,24 @@ def test_server_leaves_other_threads_graph_mode_alone(engine):
     before = bt.get_options()["use_graph"]
     _serve(40, 11, 1 << 28, hi_log2=15, engine=engine)
     assert bt.get_options()["use_graph"] == before
+
+
+@pytest.mark.gpu
+def test_native_loop_splits_groups_larger_than_the_budget():
+    # 1 MiB of device memory and 200,000 req/s of requests up to 2^14 keys:
+    # the requests that wait together form packed groups larger than the
+    # whole budget, which the native loop splits until the head fits.  Every
+    # result must still be the oracle's.
+    srv, stats, outs, reqs, pool, pool_v, torch = _serve(300, 13, 1 << 20, hi_log2=14, rate=200000.0)
+    assert stats["peak_device_bytes"] <= 1 << 20
+    probe = type(srv).__new__(type(srv))
+    probe.rings, probe.ring_pos = srv.rings, {k: 0 for k in srv.rings}
+    for i, (kind, n, has_v) in enumerate(reqs):
+        src = type(srv)._src(probe, kind, n)
+        k_in, v_in = pool[src:src + n], pool_v[src:src + n]
+        got_k, got_v = outs[i]
+        if has_v:
+            wk, wv = oracle.merge_sort_pairs(k_in, v_in)
+            assert np.array_equal(got_k, wk) and np.array_equal(got_v, wv), i
+        else:
+            assert np.array_equal(got_k, oracle.merge_sort(k_in)), i
