@@ -445,7 +445,7 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
             const KeyMapHost& mo = (i + 1 == pl.launches.size() && !separate) ? km.out : ident;
             const int pmode = pio ? ((i == 0 ? 1 : 0) | (i + 1 == pl.launches.size() ? 2 : 0)) : 0;
             if (pmode) {
-                const uint32_t pf = (pmode == 2 && pe.opt.l2_prefetch > 0)
+                const uint32_t pf = pe.opt.l2_prefetch > 0
                                         ? (uint32_t)(pe.opt.l2_prefetch * ds.tile_blocks[pl.cfg] * ds.num_sms)
                                         : 0u;
                 e = launch_tile_pairs(pl.cfg, pmode, (uint64_t*)base, hi, hP, ntiles, *pio, pf, s);

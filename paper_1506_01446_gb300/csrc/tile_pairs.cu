@@ -115,6 +115,11 @@ k_tile_pairs(uint64_t* __restrict__ comp, uint32_t hi, const __grid_constant__ T
     T t;
     if constexpr (MODE & 1) {
         load_pairs<LOG_R, LOG_T>(t, pio, hi, P.io[0], g0, x);
+        // the caller's keys of the tile one resident wave ahead (composite
+        // positions are key positions; bulk prefetches need 16-byte aligned
+        // addresses, so only for a 16-byte aligned key array)
+        if ((reinterpret_cast<uintptr_t>(pio.keys_in) & 15u) == 0)
+            prefetch_tile_l2<uint32_t, LOG_T>(pio.keys_in, 0, hi, P, pf_dist, 0);
     } else {
         if (interior)
             t.load_global_interior(comp, P.io[0], g0, x, ident);
