@@ -687,7 +687,10 @@ def main():
                             "kernel": bt.KIND_NAMES[dom], "launches_per_step": len(per_kind[dom]) // args.steps,
                             "avg_launch_ms": avg_ms, "peak_source": peak_src,
                             "share": {bt.KIND_NAMES[k]: v / sum(tot.values()) for k, v in tot.items()},
-                            "by_round_shape": line_shapes}
+                            "by_round_shape": line_shapes,
+                            "launch_timing": "CUDA events between the launches of the plan run as one sequence on "
+                                             "the launching stream (the timed graph runs the leading launches as "
+                                             "two concurrent tile ranges, the same kernels over the same tiles)"}
 
         # end to end through the C ABI on host buffers: one batched call
         # (bitonic_sort_u32_host_batch) sorts the K steps' arrays; every step

@@ -273,9 +273,14 @@ typedef struct {
                              reads back exactly the slots it wrote waits at a warp barrier, the
                              others at a CTA barrier (default); 1 = a CTA barrier after every
                              transpose */
+    int split_log2;       /* graph-captured sorts: the leading tile launches whose strides stay
+                             below 2^(k - split_log2) (every launch before the last split_log2
+                             phases) run as 2^split_log2 concurrent tile ranges, one contiguous
+                             part of the array each, on library streams that fork from and
+                             join back to the sort's stream; 0 = off, 1 (default) or 2 */
 } bitonic_options;
 
-/* Process-wide options (defaults: all zero except use_graph = 1 and l2_prefetch = 1). */
+/* Process-wide options (defaults: all zero except use_graph = 1, l2_prefetch = 1 and split_log2 = 1). */
 bitonic_status bitonic_set_options(const bitonic_options *opt);
 bitonic_status bitonic_get_options(bitonic_options *opt);
 

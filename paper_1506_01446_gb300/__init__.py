@@ -52,7 +52,7 @@ class Options(ctypes.Structure):
                 ("global_bits", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("keys_per_thread_log2", ctypes.c_int), ("io_direct", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("min_row_log2", ctypes.c_int), ("l2_prefetch", ctypes.c_int),
-                ("pipeline", ctypes.c_int), ("round_sync", ctypes.c_int)]
+                ("pipeline", ctypes.c_int), ("round_sync", ctypes.c_int), ("split_log2", ctypes.c_int)]
 
 
 class SegOptions(ctypes.Structure):
@@ -304,12 +304,13 @@ def get_options() -> dict:
 
 def set_options(variant=None, tile_log2=None, global_bits=None, use_graph=None,
                 keys_per_thread_log2=None, io_direct=None, pipeline=None, l2_prefetch=None,
-                min_row_log2=None, ctas_per_sm=None, round_sync=None):
+                min_row_log2=None, ctas_per_sm=None, round_sync=None, split_log2=None):
     cur = get_options()
     for k, v in (("variant", variant), ("tile_log2", tile_log2), ("global_bits", global_bits),
                  ("use_graph", use_graph), ("keys_per_thread_log2", keys_per_thread_log2),
                  ("io_direct", io_direct), ("pipeline", pipeline), ("l2_prefetch", l2_prefetch),
-                 ("min_row_log2", min_row_log2), ("ctas_per_sm", ctas_per_sm), ("round_sync", round_sync)):
+                 ("min_row_log2", min_row_log2), ("ctas_per_sm", ctas_per_sm), ("round_sync", round_sync),
+                 ("split_log2", split_log2)):
         if v is not None:
             cur[k] = int(v)
     _check(load().bitonic_set_options(ctypes.byref(Options(**cur))), "bitonic_set_options")

@@ -32,6 +32,7 @@ constexpr int kDevBadOffsets = 1;
 constexpr int kDevTimeout = 2;
 
 constexpr size_t kMaxGraphs = 64;
+constexpr int kMaxSplit = 4;  // most concurrent tile ranges of a split sort (Options::split_log2 <= 2)
 // Bound of each wait of the long-segment sort for a segment's previous pass
 // (polls about 128 ns apart: about half a second).
 constexpr uint32_t kLongWaitSpins = 1u << 22;
@@ -117,7 +118,7 @@ Options resolve_options(int key_bytes, int k)
 uint64_t options_code(const Options& o)
 {
     const int f[] = {o.variant, o.tile_log2, o.keys_per_thread_log2, o.global_bits, o.io_direct,
-                     o.pipeline, o.l2_prefetch, o.min_row_log2, o.ctas_per_sm, o.round_sync};
+                     o.pipeline, o.l2_prefetch, o.min_row_log2, o.ctas_per_sm, o.round_sync, o.split_log2};
     uint64_t c = 0;
     for (int v : f) c = (c << 5) | uint64_t(v & 31);
     return c;
@@ -139,6 +140,9 @@ struct DeviceState {
     int pipe_blocks[kNumTileCfgs] = {};  // resident pipelined CTAs per SM, per configuration
     int tile_blocks[kNumTileCfgs] = {};  // resident tile CTAs per SM, per configuration
     int* status = nullptr;               // device status word shared by every stream
+    // forked launch ranges of graph-captured sorts (Options::split_log2)
+    cudaStream_t split[kMaxSplit - 1] = {};
+    cudaEvent_t split_ev[kMaxSplit] = {};
     // packed segment tiles by class: 16K keys, 8K composites (pairs), 8K keys
     TileParamsBig* seg_descs[3] = {nullptr, nullptr, nullptr};
     // Segments longer than one tile (keys): the launch plans of sorts of
@@ -188,6 +192,8 @@ bitonic_status device_state(DeviceState** out)
         for (int c = 0; c < kNumTileCfgs; ++c) BT_CK(tile_blocks_per_sm(c, &ds.tile_blocks[c]));
         BT_CK(seg_init_attributes());
         BT_CK(cudaStreamCreateWithFlags(&ds.capture, cudaStreamNonBlocking));
+        for (cudaStream_t& t : ds.split) BT_CK(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : ds.split_ev) BT_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         BT_CK(cudaMalloc(&ds.status, sizeof(int)));
         BT_CK(cudaMemset(ds.status, 0, sizeof(int)));
         for (int which = 0; which < 3; ++which) {
@@ -424,7 +430,70 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
         cudaError_t e = launch_keymap(key_bytes, base, lo, hi, km.in, s);
         if (e != cudaSuccess) return cuda_fail(e, "key map launch");
     }
-    for (size_t i = 0; i < pl.launches.size(); ++i) {
+    const size_t nl = pl.launches.size();
+    auto pmode_of = [&](size_t i) { return pio ? ((i == 0 ? 1 : 0) | (i + 1 == nl ? 2 : 0)) : 0; };
+    auto live_tiles = [&](const Launch& L) {  // tiles wholly past the last key have nothing to do
+        const TileParamsBig& D = pl.descs[L.desc];
+        uint32_t ntiles = L.grid;
+        if (D.contiguous) {
+            const uint64_t live = ((uint64_t)hi + (1u << D.m) - 1) >> D.m;
+            if (live < ntiles) ntiles = (uint32_t)live;
+        }
+        return ntiles;
+    };
+    const uint32_t wave = (uint32_t)(pe.opt.l2_prefetch * ds.tile_blocks[pl.cfg] * ds.num_sms);
+    // Concurrent tile ranges (Options::split_log2), only while the launches
+    // are captured into a graph, where the forked streams become parallel
+    // branches: a launch whose strides all lie below bit k - split_log2
+    // works within blocks of 2^(k - split_log2) positions, and since a
+    // tile's index fills the position bits outside the tile from the lowest
+    // up, part q of the array is tile range [q T / S, (q + 1) T / S).  A run
+    // of such launches goes to S streams, each taking its part through the
+    // whole run; the streams join back before the next launch.  Two parts
+    // (the default): 2^28 keys 12.04 against 12.12 ms, 2^24 0.565 against
+    // 0.626 ms (each launch's last wave overlaps the other part's next
+    // launch).  Four parts were slower (2^28: 13.02 ms), and so was a second
+    // part started one launch behind the first (12.12 ms).
+    int S = 1;
+    if (pe.opt.split_log2 > 0 && pe.opt.variant == 0 && !steps && !piped && !events) {
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        BT_CK(cudaStreamIsCapturing(s, &cst));
+        if (cst == cudaStreamCaptureStatusActive) S = 1 << pe.opt.split_log2;
+    }
+    auto splittable = [&](size_t i) {
+        const Launch& L = pl.launches[i];
+        return L.kind != KIND_STEP && pmode_of(i) == 0 && L.hi < pl.k - pe.opt.split_log2 &&
+               L.grid % (uint32_t)S == 0;
+    };
+    for (size_t i = 0; i < nl;) {
+        size_t run_end = i;
+        if (S > 1)
+            while (run_end < nl && splittable(run_end)) ++run_end;
+        if (run_end - i >= 2) {
+            BT_CK(cudaEventRecord(ds.split_ev[0], s));
+            for (int q = 1; q < S; ++q) BT_CK(cudaStreamWaitEvent(ds.split[q - 1], ds.split_ev[0], 0));
+            for (int q = 0; q < S; ++q) {
+                cudaStream_t sq = q == 0 ? s : ds.split[q - 1];
+                for (size_t a = i; a < run_end; ++a) {
+                    const Launch& L = pl.launches[a];
+                    const TileParams* hP = L.small ? &pl.small[L.desc] : nullptr;
+                    const TileParamsBig* dP = L.small ? nullptr : pe.d_descs + L.desc;
+                    const uint32_t per = L.grid / (uint32_t)S, ntiles = live_tiles(L);
+                    const uint32_t t0 = (uint32_t)q * per, t1 = std::min(t0 + per, ntiles);
+                    if (t1 <= t0) continue;
+                    const KeyMapHost& mi = (a == 0 && !separate) ? km.in : ident;
+                    const KeyMapHost& mo = (a + 1 == nl && !separate) ? km.out : ident;
+                    cudaError_t e = launch_tile(pl.cfg, base, lo, hi, hP, dP, t1 - t0, mi, mo, sq, wave, t0);
+                    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+                }
+            }
+            for (int q = 1; q < S; ++q) {
+                BT_CK(cudaEventRecord(ds.split_ev[q], ds.split[q - 1]));
+                BT_CK(cudaStreamWaitEvent(s, ds.split_ev[q], 0));
+            }
+            i = run_end;
+            continue;
+        }
         const Launch& L = pl.launches[i];
         if (events) BT_CK(cudaEventRecord(events[i], s));
         if (kinds) kinds[i] = L.kind;
@@ -434,34 +503,24 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
         } else {
             const TileParams* hP = L.small ? &pl.small[L.desc] : nullptr;
             const TileParamsBig* dP = L.small ? nullptr : pe.d_descs + L.desc;
-            const TileParamsBig& D = pl.descs[L.desc];
-            uint32_t ntiles = L.grid;
-            if (D.contiguous) {  // tiles wholly past the last key have nothing to do
-                const uint64_t live = ((uint64_t)hi + (1u << D.m) - 1) >> D.m;
-                if (live < ntiles) ntiles = (uint32_t)live;
-            }
+            const uint32_t ntiles = live_tiles(L);
             // The key maps are fused into the first load and the last store.
             const KeyMapHost& mi = (i == 0 && !separate) ? km.in : ident;
-            const KeyMapHost& mo = (i + 1 == pl.launches.size() && !separate) ? km.out : ident;
-            const int pmode = pio ? ((i == 0 ? 1 : 0) | (i + 1 == pl.launches.size() ? 2 : 0)) : 0;
+            const KeyMapHost& mo = (i + 1 == nl && !separate) ? km.out : ident;
+            const int pmode = pmode_of(i);
             if (pmode) {
-                const uint32_t pf = pe.opt.l2_prefetch > 0
-                                        ? (uint32_t)(pe.opt.l2_prefetch * ds.tile_blocks[pl.cfg] * ds.num_sms)
-                                        : 0u;
-                e = launch_tile_pairs(pl.cfg, pmode, (uint64_t*)base, hi, hP, ntiles, *pio, pf, s);
+                e = launch_tile_pairs(pl.cfg, pmode, (uint64_t*)base, hi, hP, ntiles, *pio, wave, s);
             } else if (piped) {
                 const int per_sm = ds.pipe_blocks[pl.cfg];
                 uint64_t g = (uint64_t)per_sm * ds.num_sms;
                 const uint32_t grid = (uint32_t)(g < ntiles ? g : ntiles);
                 e = launch_pipe(pe.opt.pipeline, pl.cfg, base, lo, hi, hP, dP, ntiles, grid, mi.b, mo.b, status, s);
             } else {
-                const uint32_t pf = pe.opt.l2_prefetch > 0
-                                        ? (uint32_t)(pe.opt.l2_prefetch * ds.tile_blocks[pl.cfg] * ds.num_sms)
-                                        : 0u;
-                e = launch_tile(pl.cfg, base, lo, hi, hP, dP, ntiles, mi, mo, s, pf);
+                e = launch_tile(pl.cfg, base, lo, hi, hP, dP, ntiles, mi, mo, s, wave);
             }
         }
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        ++i;
     }
     if (events) BT_CK(cudaEventRecord(events[pl.launches.size()], s));
     if (separate) {
@@ -1169,6 +1228,7 @@ bitonic_status bitonic_set_options(const bitonic_options* opt)
     g_opt.min_row_log2 = (opt->min_row_log2 < 0 || opt->min_row_log2 > 12) ? 0 : opt->min_row_log2;
     g_opt.ctas_per_sm = (opt->ctas_per_sm == 2 || opt->ctas_per_sm == 3) ? opt->ctas_per_sm : 0;
     g_opt.round_sync = opt->round_sync ? 1 : 0;
+    g_opt.split_log2 = (opt->split_log2 >= 0 && opt->split_log2 <= 2) ? opt->split_log2 : 0;
     return BITONIC_OK;
 }
 
@@ -1263,6 +1323,7 @@ bitonic_status bitonic_get_options(bitonic_options* opt)
     opt->min_row_log2 = g_opt.min_row_log2;
     opt->ctas_per_sm = g_opt.ctas_per_sm;
     opt->round_sync = g_opt.round_sync;
+    opt->split_log2 = g_opt.split_log2;
     return BITONIC_OK;
 }
 

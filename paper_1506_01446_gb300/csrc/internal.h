@@ -62,6 +62,7 @@ struct Options {
     int ctas_per_sm = 0;
     int pipeline = 0;
     int round_sync = 0;   // 0: warp barriers where a transpose keeps each warp's slots; 1: CTA barriers
+    int split_log2 = 1;   // graph captures: the leading launches as 2^split_log2 concurrent tile ranges
 };
 
 // Builds the launch sequence for a sort of n keys of key_bytes bytes.

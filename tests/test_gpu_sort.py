@@ -1,5 +1,7 @@
 """GPU parity: the CUDA path through the C ABI, bit-exact against the CPU
 oracle on seeded inputs (sorting has a unique result, so no tolerance)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -26,13 +28,14 @@ def to_host(t) -> np.ndarray:
     return t.cpu().numpy().view(np.uint32)
 
 
+LIBRARY_DEFAULTS = bt.get_options() if os.path.exists(bt.LIB_PATH) else {}
+
+
 @pytest.fixture(autouse=True)
 def default_options():
-    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1, keys_per_thread_log2=0, pipeline=0,
-                   l2_prefetch=1, min_row_log2=0, ctas_per_sm=0)
+    bt.set_options(**LIBRARY_DEFAULTS)
     yield
-    bt.set_options(variant=0, tile_log2=0, global_bits=0, use_graph=1, keys_per_thread_log2=0, pipeline=0,
-                   l2_prefetch=1, min_row_log2=0, ctas_per_sm=0)
+    bt.set_options(**LIBRARY_DEFAULTS)
     assert bt.last_device_error() == bt.OK
 
 
@@ -645,3 +648,45 @@ def test_maximum_size_properties():
         del t, flipped
     del src
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("split", [1, 2])
+def test_split_tile_ranges_agree_with_oracle(split):
+    # The leading launches of a graph-captured sort as 2 or 4 concurrent
+    # tile ranges: sizes with several global passes, a ragged tail with
+    # tiles past the last key, an off-boundary front, both directions; pairs
+    # (whose first and last launches stay whole) and 8-byte keys; and a sort
+    # captured inside a caller's graph.
+    bt.set_options(split_log2=split)
+    for n in [1 << 16, (1 << 20) + 3, 1 << 22, 10_000_019]:
+        keys = workloads.uniform_u32(n, seed=n + 5)
+        check_keys(keys, True)
+        check_keys(keys, False, 1)
+    n = (1 << 21) + 5
+    keys = (workloads.uniform_u32(n, seed=3) >> np.uint32(20)).astype(np.uint32)
+    vals = workloads.uniform_u32(n, seed=4)
+    wk, wv = oracle.merge_sort_pairs(keys, vals, False)
+    tk, tv = to_dev(keys), to_dev(vals)
+    bt.sort_pairs_(tk, tv, False)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(tk), wk) and np.array_equal(to_host(tv), wv)
+    k64 = workloads.typed_keys("uint64", (1 << 20) + 7, seed=5, specials=True)
+    check_typed(k64, True)
+    check_typed(k64, False, 1)
+    keys = workloads.uniform_u32((1 << 20) + 3, seed=6)
+    src = to_dev(keys)
+    t = torch.empty_like(src)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        t.copy_(src)
+        bt.sort_(t)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        t.copy_(src)
+        bt.sort_(t)
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(t), oracle.merge_sort(keys))
