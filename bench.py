@@ -634,7 +634,7 @@ def main():
                                   else "input restored by a copy before each step"),
                    "parallelism": f"replicas x{world}",
                    "plan": info, "tuned": tuned},
-        "gpu_launches": info["launches"] * args.steps,
+        "gpu_launches": bt.graph_kernels(n) * args.steps,
         "clocks": clk.summary(),
     }
 

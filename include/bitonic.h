@@ -349,6 +349,16 @@ bitonic_status bitonic_plan_info(size_t n, int pairs, int *launches, int *hbm_pa
                                  int *fused_steps, int *global_steps);
 
 /*
+ * Kernels one graph-replayed bitonic_sort_u32 (pairs != 0:
+ * bitonic_sort_pairs_u32) of n keys launches under the current options:
+ * bitonic_plan_info's launches with every launch of a split run (option
+ * split_log2) counted once per tile range, which the unsplit sequence of
+ * bitonic_sort_u32_profiled does not have.  A key array off a 16-byte
+ * boundary may add a launch.  BITONIC_ERR_INVALID for a NULL kernels.
+ */
+bitonic_status bitonic_graph_kernels(size_t n, int pairs, int *kernels);
+
+/*
  * Same as bitonic_sort_u32 but launched without a graph, recording
  * events[i] on `stream` before launch i of the sequence and events[L] after
  * the last one (L = launches of bitonic_plan_info).  nevents must be >= L + 1.

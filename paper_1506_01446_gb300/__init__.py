@@ -32,7 +32,7 @@ EXPORTS = (
     "bitonic_set_class_options", "bitonic_sort_i32", "bitonic_sort_f32", "bitonic_sort_u64", "bitonic_sort_i64",
     "bitonic_sort_f64", "bitonic_sort_u32_host", "bitonic_sort_u32_host_batch",
     "bitonic_sort_segmented_u32_dir", "bitonic_sort_segmented_pairs_u32_dir", "bitonic_set_thread_graphs",
-    "bitonic_debug_set_wait", "bitonic_set_segmented_options", "bitonic_serve_run",
+    "bitonic_debug_set_wait", "bitonic_set_segmented_options", "bitonic_serve_run", "bitonic_graph_kernels",
 )
 
 # torch dtype name -> C entry point of the keys-only sorts (uint64 keys may be
@@ -116,6 +116,7 @@ def load() -> ctypes.CDLL:
     lib.bitonic_set_options.argtypes = [ctypes.POINTER(Options)]
     lib.bitonic_get_options.argtypes = [ctypes.POINTER(Options)]
     lib.bitonic_plan_info.argtypes = [sz, i32, pint, pint, pint, pint]
+    lib.bitonic_graph_kernels.argtypes = [sz, i32, pint]
     lib.bitonic_sort_u32_profiled.argtypes = [vp, sz, i32, vp, ctypes.POINTER(vp), i32, pint]
     lib.bitonic_debug_plan.argtypes = [sz, i32, pint, i32, vp, i32]
     lib.bitonic_debug_desc_size.argtypes = []
@@ -363,6 +364,13 @@ def plan_info(n: int, pairs: bool = False) -> dict:
     _check(load().bitonic_plan_info(int(n), int(bool(pairs)), *[ctypes.byref(x) for x in out]),
            "bitonic_plan_info")
     return dict(zip(("launches", "hbm_passes", "fused_steps", "global_steps"), (x.value for x in out)))
+
+
+def graph_kernels(n: int, pairs: bool = False) -> int:
+    """Kernels one graph-replayed sort of n keys launches (bitonic_graph_kernels)."""
+    out = ctypes.c_int()
+    _check(load().bitonic_graph_kernels(int(n), int(bool(pairs)), ctypes.byref(out)), "bitonic_graph_kernels")
+    return out.value
 
 
 def desc_dtype():

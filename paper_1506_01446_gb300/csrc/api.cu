@@ -403,6 +403,25 @@ bool pairs_fused(const Plan& pl, const Options& o)
            pl.launches.front().small && pl.launches.back().small;
 }
 
+// End of the run of launches from launch i that a graph-captured sort
+// splits into S concurrent tile ranges (see enqueue_plan); i when the launch
+// at i starts no such run (runs are at least two launches long).  pairs_io:
+// the plan's first and last launches build and split pair composites and
+// stay whole.
+size_t split_run_end(const Plan& pl, size_t i, int S, int split_log2, bool pairs_io)
+{
+    if (S < 2) return i;
+    const size_t nl = pl.launches.size();
+    size_t e = i;
+    while (e < nl) {
+        const Launch& L = pl.launches[e];
+        const bool edge = pairs_io && (e == 0 || e + 1 == nl);
+        if (L.kind == KIND_STEP || edge || L.hi >= pl.k - split_log2 || L.grid % (uint32_t)S != 0) break;
+        ++e;
+    }
+    return e - i >= 2 ? e : i;
+}
+
 bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* base, uint32_t lo, uint32_t hi,
                             const KeyMaps& km, int key_bytes, int* status, cudaStream_t s, cudaEvent_t* events,
                             int* kinds, const PairIo* pio = nullptr)
@@ -460,16 +479,9 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
         BT_CK(cudaStreamIsCapturing(s, &cst));
         if (cst == cudaStreamCaptureStatusActive) S = 1 << pe.opt.split_log2;
     }
-    auto splittable = [&](size_t i) {
-        const Launch& L = pl.launches[i];
-        return L.kind != KIND_STEP && pmode_of(i) == 0 && L.hi < pl.k - pe.opt.split_log2 &&
-               L.grid % (uint32_t)S == 0;
-    };
     for (size_t i = 0; i < nl;) {
-        size_t run_end = i;
-        if (S > 1)
-            while (run_end < nl && splittable(run_end)) ++run_end;
-        if (run_end - i >= 2) {
+        const size_t run_end = split_run_end(pl, i, S, pe.opt.split_log2, pio != nullptr);
+        if (run_end > i) {
             BT_CK(cudaEventRecord(ds.split_ev[0], s));
             for (int q = 1; q < S; ++q) BT_CK(cudaStreamWaitEvent(ds.split[q - 1], ds.split_ev[0], 0));
             for (int q = 0; q < S; ++q) {
@@ -1352,6 +1364,41 @@ bitonic_status bitonic_plan_info(size_t n, int pairs, int* launches, int* hbm_pa
     if (hbm_passes) *hbm_passes = p.hbm_passes;
     if (fused_steps) *fused_steps = p.fused_steps;
     if (global_steps) *global_steps = p.global_steps;
+    return BITONIC_OK;
+}
+
+bitonic_status bitonic_graph_kernels(size_t n, int pairs, int* kernels)
+{
+    if (!kernels) return BITONIC_ERR_INVALID;
+    if (n > kMaxKeys) return BITONIC_ERR_UNSUPPORTED;
+    *kernels = 0;
+    if (n <= 1) return BITONIC_OK;
+    Options o;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        uint64_t N = 2;
+        int k = 1;
+        while (N < n) { N <<= 1; ++k; }
+        o = resolve_options(pairs ? 8 : 4, k);
+    }
+    Plan p = make_plan(n, pairs ? 8 : 4, o);
+    if (!p.ok) return BITONIC_ERR_UNSUPPORTED;
+    const bool steps = p.launches[0].kind == KIND_STEP;
+    const bool fused = pairs && pairs_fused(p, o);
+    const int S = (o.split_log2 > 0 && o.variant == 0 && !steps && !o.pipeline) ? 1 << o.split_log2 : 1;
+    int count = 0;
+    for (size_t i = 0; i < p.launches.size();) {
+        const size_t e = split_run_end(p, i, S, o.split_log2, fused);
+        if (e > i) {
+            count += (int)(e - i) * S;
+            i = e;
+        } else {
+            ++count;
+            ++i;
+        }
+    }
+    if (pairs) count += fused ? gather_launches((uint32_t)n) : 3;
+    *kernels = count;
     return BITONIC_OK;
 }
 

@@ -172,3 +172,34 @@ def test_round_shapes_cover_every_step():
     assert sum(shapes[0]) == 14 * 15 // 2
     assert all(sum(s) <= 14 for s in shapes[1:])
     assert len(shapes) == bt.plan_info(1 << 28)["launches"]
+
+
+def test_graph_kernels_count_the_split_ranges():
+    # A graph-captured sort splits every run of at least two launches whose
+    # strides stay below bit k - split_log2 into 2^split_log2 tile ranges,
+    # one kernel each; the plan itself is unchanged.
+    saved = bt.get_options()
+    try:
+        for split in (0, 1, 2):
+            bt.set_options(split_log2=split)
+            for k in (16, 20, 24, 28):
+                plan = bt.debug_plan(1 << k)
+                his = [la[2] for la in plan["launches"]]
+                his_ok = [h < k - split and (1 << (k - 14)) % (1 << split) == 0 for h in his]
+                want, i = 0, 0
+                while i < len(his):
+                    j = i
+                    while split and j < len(his) and his_ok[j]:
+                        j += 1
+                    if j - i >= 2:
+                        want += (j - i) << split
+                        i = j
+                    else:
+                        want += 1
+                        i += 1
+                assert bt.graph_kernels(1 << k) == want, (split, k)
+                assert bt.plan_info(1 << k)["launches"] == len(his)
+        bt.set_options(split_log2=1)
+        assert bt.graph_kernels(1 << 28) == 55 and bt.plan_info(1 << 28)["launches"] == 28
+    finally:
+        bt.set_options(**saved)
