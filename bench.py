@@ -717,7 +717,9 @@ def main():
             return link
 
         link = measure_link()
-        bt.sort_host_batch([host_in] * 2, host_out)  # warm-up: buffers, streams, plan
+        # warm-up: buffers, streams, plan, and the graphs of the arrays between
+        # the first and the last (one per device buffer)
+        bt.sort_host_batch([host_in] * 4, [host_out[i % 2] for i in range(4)])
         torch.cuda.synchronize()
         # five timed batch calls, the median reported: the host link of a
         # shared machine occasionally slows for a while on its own (the link

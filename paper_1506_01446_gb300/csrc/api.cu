@@ -649,7 +649,7 @@ cudaError_t launch_plan_tiles(const DeviceState& ds, const PlanEntry& pe, size_t
 // array's upload ahead of this array's download.
 constexpr int kHostUpload = 1, kHostCompute = 2, kHostDownload = 4;
 
-bitonic_status enqueue_host_sort(const DeviceState& ds, const PlanEntry& pe, const uint32_t* in, uint32_t* out,
+bitonic_status enqueue_host_sort(DeviceState& ds, const PlanEntry& pe, const uint32_t* in, uint32_t* out,
                                  size_t n, const KeyMaps& km, uint32_t* dev, cudaStream_t up, cudaStream_t comp,
                                  cudaStream_t down, cudaEvent_t* ev_in, cudaEvent_t* ev_out, int n_up, int n_down,
                                  int phases = kHostUpload | kHostCompute | kHostDownload)
@@ -675,7 +675,18 @@ bitonic_status enqueue_host_sort(const DeviceState& ds, const PlanEntry& pe, con
             BT_CK(cudaMemcpyAsync(dev + a, in + a, (b - a) * sizeof(uint32_t), cudaMemcpyHostToDevice, up));
             BT_CK(cudaEventRecord(ev_in[c], up));
         }
-    if (phases & kHostCompute) {
+    if ((phases & kHostCompute) && nin == 1 && nout == 1 && L > 1) {
+        // one upload and one download: the whole plan as the cached graph of
+        // the device sort of these keys (with its leading launches split in
+        // concurrent halves), replayed on the compute stream
+        BT_CK(cudaStreamWaitEvent(comp, ev_in[0], 0));
+        const GraphKey key{0, (uint64_t)n, km.in.b != 0 ? 1 : 0, (uintptr_t)dev, 0, 0, 0, 0, 0, options_code(pe.opt), 0};
+        bitonic_status st = run_graphed(ds, key, comp, [&](cudaStream_t cs) {
+            return enqueue_plan(ds, pe, dev, 0, (uint32_t)n, km, 4, ds.status, cs, nullptr, nullptr);
+        });
+        if (st != BITONIC_OK) return st;
+        BT_CK(cudaEventRecord(ev_out[0], comp));
+    } else if (phases & kHostCompute) {
         for (uint32_t c = 0; c < nin; ++c) {
             BT_CK(cudaStreamWaitEvent(comp, ev_in[c], 0));
             const bool also_last = L == 1;

@@ -592,6 +592,14 @@ def test_host_buffer_batch(ascending):
     torch.cuda.synchronize()
     for i, k in enumerate(keys):
         assert np.array_equal(outs[i].numpy().view(np.uint32), oracle.merge_sort(k, ascending)), sizes[i]
+    # the same call again: the arrays between the first and the last replay
+    # the device-sort graphs captured the first time (one per device buffer)
+    ins = [host_tensor(k) for k in keys]
+    outs = [host_tensor(np.zeros(n, np.uint32)) for n in sizes]
+    bt.sort_host_batch(ins, outs, ascending)
+    torch.cuda.synchronize()
+    for i, k in enumerate(keys):
+        assert np.array_equal(outs[i].numpy().view(np.uint32), oracle.merge_sort(k, ascending)), sizes[i]
     shared = host_tensor(np.zeros(1 << 20, np.uint32))
     a, b = workloads.uniform_u32(1 << 20, seed=7), workloads.uniform_u32(1 << 20, seed=8)
     bt.sort_host_batch([host_tensor(a), host_tensor(np.zeros(3, np.uint32)), host_tensor(b)],
