@@ -462,8 +462,8 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
     };
     const uint32_t wave = (uint32_t)(pe.opt.l2_prefetch * ds.tile_blocks[pl.cfg] * ds.num_sms);
     // Concurrent tile ranges (Options::split_log2), only while the launches
-    // are captured into a graph, where the forked streams become parallel
-    // branches: a launch whose strides all lie below bit k - split_log2
+    // are captured into one of the library's graphs, where the forked
+    // streams become parallel branches: a launch whose strides all lie below bit k - split_log2
     // works within blocks of 2^(k - split_log2) positions, and since a
     // tile's index fills the position bits outside the tile from the lowest
     // up, part q of the array is tile range [q T / S, (q + 1) T / S).  A run
@@ -473,8 +473,12 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
     // 0.626 ms (each launch's last wave overlaps the other part's next
     // launch).  Four parts were slower (2^28: 13.02 ms), and so was a second
     // part started one launch behind the first (12.12 ms).
+    // Only the library's own captures split (s is then ds.capture): they
+    // begin and end inside one call under the library's lock, whereas a
+    // stream forked into a caller's capture would stay part of it until the
+    // caller ends it, and could not join another capture meanwhile.
     int S = 1;
-    if (pe.opt.split_log2 > 0 && pe.opt.variant == 0 && !steps && !piped && !events) {
+    if (pe.opt.split_log2 > 0 && pe.opt.variant == 0 && !steps && !piped && !events && s == ds.capture) {
         cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
         BT_CK(cudaStreamIsCapturing(s, &cst));
         if (cst == cudaStreamCaptureStatusActive) S = 1 << pe.opt.split_log2;

@@ -664,7 +664,8 @@ def test_split_tile_ranges_agree_with_oracle(split):
     # tile ranges: sizes with several global passes, a ragged tail with
     # tiles past the last key, an off-boundary front, both directions; pairs
     # (whose first and last launches stay whole) and 8-byte keys; and a sort
-    # captured inside a caller's graph.
+    # captured inside a caller's graph (which stays unsplit), followed by a
+    # split sort on another stream while that graph still exists.
     bt.set_options(split_log2=split)
     for n in [1 << 16, (1 << 20) + 3, 1 << 22, 10_000_019]:
         keys = workloads.uniform_u32(n, seed=n + 5)
@@ -698,3 +699,10 @@ def test_split_tile_ranges_agree_with_oracle(split):
     g.replay()
     torch.cuda.synchronize()
     assert np.array_equal(to_host(t), oracle.merge_sort(keys))
+    other = workloads.uniform_u32(1 << 22, seed=8)
+    t2 = to_dev(other)
+    s2 = torch.cuda.Stream()
+    with torch.cuda.stream(s2):
+        bt.sort_(t2)
+    s2.synchronize()
+    assert np.array_equal(to_host(t2), oracle.merge_sort(other))
