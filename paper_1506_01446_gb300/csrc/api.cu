@@ -672,10 +672,26 @@ bitonic_status enqueue_host_sort(DeviceState& ds, const PlanEntry& pe, const uin
     auto tiles_of = [&](uint32_t c, uint32_t nch) { return (uint32_t)((uint64_t)live * c / nch); };
     auto keys_of = [&](uint32_t t) { return std::min<size_t>((size_t)t << m, n); };
     const KeyMapHost ident;
+    // With C = nin a power of two dividing the T tiles of every launch,
+    // upload chunk c is tiles [c T / C, (c + 1) T / C): part c of the sort's
+    // positions.  A launch whose strides all lie below bit k - log2(C) works
+    // within those parts (a tile's index fills the position bits outside the
+    // tile from the lowest up), so the leading run of such launches runs on
+    // each chunk as soon as it has arrived, overlapping the rest of the
+    // upload; the other launches follow over all tiles.
+    const uint32_t T = pl.launches[0].grid;
+    int lc = 0;
+    while ((2u << lc) <= nin) ++lc;
+    size_t prefix = 0;
+    if (nin > 1 && (1u << lc) == nin && T % nin == 0 && L > 1)
+        while (prefix + 1 < L && pl.launches[prefix].kind != KIND_STEP && pl.launches[prefix].hi < pl.k - lc)
+            ++prefix;
+    auto part_tiles = [&](uint32_t c) { return std::min<uint32_t>((uint32_t)((uint64_t)T * c / nin), live); };
+    auto in_tiles = [&](uint32_t c) { return prefix ? part_tiles(c) : tiles_of(c, nin); };
     // upload in chunks; the tile sort (launch 0) follows each chunk
     if (phases & kHostUpload)
         for (uint32_t c = 0; c < nin; ++c) {
-            const size_t a = keys_of(tiles_of(c, nin)), b = keys_of(tiles_of(c + 1, nin));
+            const size_t a = keys_of(in_tiles(c)), b = keys_of(in_tiles(c + 1));
             BT_CK(cudaMemcpyAsync(dev + a, in + a, (b - a) * sizeof(uint32_t), cudaMemcpyHostToDevice, up));
             BT_CK(cudaEventRecord(ev_in[c], up));
         }
@@ -690,6 +706,42 @@ bitonic_status enqueue_host_sort(DeviceState& ds, const PlanEntry& pe, const uin
         });
         if (st != BITONIC_OK) return st;
         BT_CK(cudaEventRecord(ev_out[0], comp));
+    } else if ((phases & kHostCompute) && prefix) {
+        for (uint32_t c = 0; c < nin; ++c) {
+            BT_CK(cudaStreamWaitEvent(comp, ev_in[c], 0));
+            const uint32_t t0 = (uint32_t)((uint64_t)T * c / nin), t1 = (uint32_t)((uint64_t)T * (c + 1) / nin);
+            if (t0 >= live) continue;  // only virtual padding in this part
+            for (size_t i = 0; i < prefix; ++i) {
+                const Launch& Li = pl.launches[i];
+                const TileParamsBig& D = pl.descs[Li.desc];
+                const uint32_t end = D.contiguous ? std::min(t1, (uint32_t)((n + (size_t(1) << D.m) - 1) >> D.m)) : t1;
+                if (end <= t0) continue;
+                cudaError_t e = launch_plan_tiles(ds, pe, i, dev, 0, (uint32_t)n, i == 0 ? km.in : ident, ident, comp,
+                                                  t0, end);
+                if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+            }
+        }
+        for (size_t i = prefix; i + 1 < L; ++i) {
+            const Launch& Li = pl.launches[i];
+            const TileParamsBig& D = pl.descs[Li.desc];
+            uint32_t ntiles = Li.grid;
+            if (D.contiguous) ntiles = std::min<uint32_t>(ntiles, (uint32_t)((n + (size_t(1) << D.m) - 1) >> D.m));
+            cudaError_t e = launch_plan_tiles(ds, pe, i, dev, 0, (uint32_t)n, ident, ident, comp, 0, ntiles);
+            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        }
+        if (last_tiled) {
+            for (uint32_t c = 0; c < nout; ++c) {
+                cudaError_t e = launch_plan_tiles(ds, pe, L - 1, dev, 0, (uint32_t)n, ident, km.out, comp,
+                                                  tiles_of(c, nout), tiles_of(c + 1, nout));
+                if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+                BT_CK(cudaEventRecord(ev_out[c], comp));
+            }
+        } else {
+            const Launch& Ll = pl.launches[L - 1];
+            cudaError_t e = launch_plan_tiles(ds, pe, L - 1, dev, 0, (uint32_t)n, ident, km.out, comp, 0, Ll.grid);
+            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+            for (uint32_t c = 0; c < nout; ++c) BT_CK(cudaEventRecord(ev_out[c], comp));
+        }
     } else if (phases & kHostCompute) {
         for (uint32_t c = 0; c < nin; ++c) {
             BT_CK(cudaStreamWaitEvent(comp, ev_in[c], 0));
