@@ -686,8 +686,27 @@ bitonic_status enqueue_host_sort(DeviceState& ds, const PlanEntry& pe, const uin
     if (nin > 1 && (1u << lc) == nin && T % nin == 0 && L > 1)
         while (prefix + 1 < L && pl.launches[prefix].kind != KIND_STEP && pl.launches[prefix].hi < pl.k - lc)
             ++prefix;
-    auto part_tiles = [&](uint32_t c) { return std::min<uint32_t>((uint32_t)((uint64_t)T * c / nin), live); };
-    auto in_tiles = [&](uint32_t c) { return prefix ? part_tiles(c) : tiles_of(c, nin); };
+    auto in_tiles = [&](uint32_t c) {
+        return prefix ? std::min<uint32_t>((uint32_t)((uint64_t)T * c / nin), live) : tiles_of(c, nin);
+    };
+    // The same at the end: with D = nout a power of two dividing T, the
+    // trailing run of launches whose strides stay below bit k - log2(D)
+    // (at least the last launch, a tile merge on contiguous tiles) runs per
+    // download chunk, and each chunk is downloaded as soon as its part is
+    // done.  L: no such run (the last launch is chunked on its own).
+    int lo2 = 0;
+    while ((2u << lo2) <= nout) ++lo2;
+    size_t suffix = L;
+    if (L > 1 && nout > 1 && (1u << lo2) == nout && T % nout == 0 && last_tiled) {
+        const size_t first_free = prefix ? prefix : 1;
+        suffix = L;
+        while (suffix > first_free && pl.launches[suffix - 1].kind != KIND_STEP &&
+               pl.launches[suffix - 1].hi < pl.k - lo2)
+            --suffix;
+    }
+    auto out_tiles = [&](uint32_t c) {
+        return suffix < L ? std::min<uint32_t>((uint32_t)((uint64_t)T * c / nout), live) : tiles_of(c, nout);
+    };
     // upload in chunks; the tile sort (launch 0) follows each chunk
     if (phases & kHostUpload)
         for (uint32_t c = 0; c < nin; ++c) {
@@ -706,62 +725,59 @@ bitonic_status enqueue_host_sort(DeviceState& ds, const PlanEntry& pe, const uin
         });
         if (st != BITONIC_OK) return st;
         BT_CK(cudaEventRecord(ev_out[0], comp));
-    } else if ((phases & kHostCompute) && prefix) {
-        for (uint32_t c = 0; c < nin; ++c) {
-            BT_CK(cudaStreamWaitEvent(comp, ev_in[c], 0));
-            const uint32_t t0 = (uint32_t)((uint64_t)T * c / nin), t1 = (uint32_t)((uint64_t)T * (c + 1) / nin);
-            if (t0 >= live) continue;  // only virtual padding in this part
-            for (size_t i = 0; i < prefix; ++i) {
-                const Launch& Li = pl.launches[i];
-                const TileParamsBig& D = pl.descs[Li.desc];
-                const uint32_t end = D.contiguous ? std::min(t1, (uint32_t)((n + (size_t(1) << D.m) - 1) >> D.m)) : t1;
-                if (end <= t0) continue;
-                cudaError_t e = launch_plan_tiles(ds, pe, i, dev, 0, (uint32_t)n, i == 0 ? km.in : ident, ident, comp,
-                                                  t0, end);
-                if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-            }
-        }
-        for (size_t i = prefix; i + 1 < L; ++i) {
-            const Launch& Li = pl.launches[i];
-            const TileParamsBig& D = pl.descs[Li.desc];
-            uint32_t ntiles = Li.grid;
-            if (D.contiguous) ntiles = std::min<uint32_t>(ntiles, (uint32_t)((n + (size_t(1) << D.m) - 1) >> D.m));
-            cudaError_t e = launch_plan_tiles(ds, pe, i, dev, 0, (uint32_t)n, ident, ident, comp, 0, ntiles);
-            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-        }
-        if (last_tiled) {
-            for (uint32_t c = 0; c < nout; ++c) {
-                cudaError_t e = launch_plan_tiles(ds, pe, L - 1, dev, 0, (uint32_t)n, ident, km.out, comp,
-                                                  tiles_of(c, nout), tiles_of(c + 1, nout));
-                if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-                BT_CK(cudaEventRecord(ev_out[c], comp));
-            }
-        } else {
-            const Launch& Ll = pl.launches[L - 1];
-            cudaError_t e = launch_plan_tiles(ds, pe, L - 1, dev, 0, (uint32_t)n, ident, km.out, comp, 0, Ll.grid);
-            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-            for (uint32_t c = 0; c < nout; ++c) BT_CK(cudaEventRecord(ev_out[c], comp));
-        }
     } else if (phases & kHostCompute) {
-        for (uint32_t c = 0; c < nin; ++c) {
-            BT_CK(cudaStreamWaitEvent(comp, ev_in[c], 0));
-            const bool also_last = L == 1;
-            cudaError_t e = launch_plan_tiles(ds, pe, 0, dev, 0, (uint32_t)n, km.in, also_last ? km.out : ident, comp,
-                                              tiles_of(c, nin), tiles_of(c + 1, nin));
-            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-            if (also_last) BT_CK(cudaEventRecord(ev_out[c], comp));
+        // tiles of launch i that hold real keys
+        auto live_of = [&](size_t i) {
+            const TileParamsBig& D = pl.descs[pl.launches[i].desc];
+            const uint32_t g = pl.launches[i].grid;
+            return D.contiguous ? std::min<uint32_t>(g, (uint32_t)((n + (size_t(1) << D.m) - 1) >> D.m)) : g;
+        };
+        // launches [i0, i1) on part c of C parts (tiles [c T / C, (c + 1) T / C))
+        auto run_part = [&](size_t i0, size_t i1, uint32_t c, uint32_t C) -> bitonic_status {
+            const uint32_t t0 = (uint32_t)((uint64_t)T * c / C), t1 = (uint32_t)((uint64_t)T * (c + 1) / C);
+            if (t0 >= live) return BITONIC_OK;  // only virtual padding in this part
+            for (size_t i = i0; i < i1; ++i) {
+                const uint32_t end = std::min(t1, live_of(i));
+                if (end <= t0) continue;
+                cudaError_t e = launch_plan_tiles(ds, pe, i, dev, 0, (uint32_t)n, i == 0 ? km.in : ident,
+                                                  i + 1 == L ? km.out : ident, comp, t0, end);
+                if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+            }
+            return BITONIC_OK;
+        };
+        size_t start = 1;
+        if (prefix) {  // the leading run on each upload chunk as soon as it has arrived
+            for (uint32_t c = 0; c < nin; ++c) {
+                BT_CK(cudaStreamWaitEvent(comp, ev_in[c], 0));
+                bitonic_status st = run_part(0, prefix, c, nin);
+                if (st != BITONIC_OK) return st;
+            }
+            start = prefix;
+        } else {  // the tile sort on each upload chunk
+            for (uint32_t c = 0; c < nin; ++c) {
+                BT_CK(cudaStreamWaitEvent(comp, ev_in[c], 0));
+                const bool also_last = L == 1;
+                cudaError_t e = launch_plan_tiles(ds, pe, 0, dev, 0, (uint32_t)n, km.in, also_last ? km.out : ident,
+                                                  comp, tiles_of(c, nin), tiles_of(c + 1, nin));
+                if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+                if (also_last) BT_CK(cudaEventRecord(ev_out[c], comp));
+            }
         }
         if (L > 1) {
-            // the middle launches over all tiles, then the last launch
-            for (size_t i = 1; i + 1 < L; ++i) {
-                const Launch& Li = pl.launches[i];
-                const TileParamsBig& D = pl.descs[Li.desc];
-                uint32_t ntiles = Li.grid;
-                if (D.contiguous) ntiles = std::min<uint32_t>(ntiles, (uint32_t)((n + (size_t(1) << D.m) - 1) >> D.m));
-                cudaError_t e = launch_plan_tiles(ds, pe, i, dev, 0, (uint32_t)n, ident, ident, comp, 0, ntiles);
+            // the middle launches over all tiles, then the trailing run per
+            // download chunk (suffix), else the last launch alone
+            const size_t tail = suffix < L ? suffix : L - 1;
+            for (size_t i = start; i < tail; ++i) {
+                cudaError_t e = launch_plan_tiles(ds, pe, i, dev, 0, (uint32_t)n, ident, ident, comp, 0, live_of(i));
                 if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
             }
-            if (last_tiled) {
+            if (suffix < L) {
+                for (uint32_t c = 0; c < nout; ++c) {
+                    bitonic_status st = run_part(suffix, L, c, nout);
+                    if (st != BITONIC_OK) return st;
+                    BT_CK(cudaEventRecord(ev_out[c], comp));
+                }
+            } else if (last_tiled) {
                 for (uint32_t c = 0; c < nout; ++c) {
                     cudaError_t e = launch_plan_tiles(ds, pe, L - 1, dev, 0, (uint32_t)n, ident, km.out, comp,
                                                       tiles_of(c, nout), tiles_of(c + 1, nout));
@@ -779,7 +795,7 @@ bitonic_status enqueue_host_sort(DeviceState& ds, const PlanEntry& pe, const uin
     if (!(phases & kHostDownload)) return BITONIC_OK;
     // download each chunk once its last launch is done
     for (uint32_t c = 0; c < nout; ++c) {
-        const size_t a = keys_of(tiles_of(c, nout)), b = keys_of(tiles_of(c + 1, nout));
+        const size_t a = keys_of(out_tiles(c)), b = keys_of(out_tiles(c + 1));
         BT_CK(cudaStreamWaitEvent(down, ev_out[c], 0));
         BT_CK(cudaMemcpyAsync(out + a, dev + a, (b - a) * sizeof(uint32_t), cudaMemcpyDeviceToHost, down));
     }
