@@ -273,9 +273,9 @@ typedef struct {
                              reads back exactly the slots it wrote waits at a warp barrier, the
                              others at a CTA barrier (default); 1 = a CTA barrier after every
                              transpose */
-    int split_log2;       /* sorts replayed from the library's cached graphs (not the launches
-                             that go straight into a caller's own capture): the leading tile
-                             launches whose strides stay
+    int split_log2;       /* sorts replayed from the library's cached graphs, and plain launches
+                             (at most two parts; not the launches that go straight into a
+                             caller's own capture): the leading tile launches whose strides stay
                              below 2^(k - split_log2) (every launch before the last split_log2
                              phases) run as 2^split_log2 concurrent tile ranges, one contiguous
                              part of the array each, on library streams that fork from and

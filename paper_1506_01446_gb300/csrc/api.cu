@@ -143,6 +143,13 @@ struct DeviceState {
     // forked launch ranges of graph-captured sorts (Options::split_log2)
     cudaStream_t split[kMaxSplit - 1] = {};
     cudaEvent_t split_ev[kMaxSplit] = {};
+    // the same for plain launches: a second stream and fork / join events
+    // per caller stream, so that sorts on different streams never share one
+    struct DirectSplit {
+        cudaStream_t stream = nullptr;
+        cudaEvent_t fork = nullptr, join = nullptr;
+    };
+    std::map<cudaStream_t, DirectSplit> direct_split;
     // packed segment tiles by class: 16K keys, 8K composites (pairs), 8K keys
     TileParamsBig* seg_descs[3] = {nullptr, nullptr, nullptr};
     // Segments longer than one tile (keys): the launch plans of sorts of
@@ -403,6 +410,13 @@ bool pairs_fused(const Plan& pl, const Options& o)
            pl.launches.front().small && pl.launches.back().small;
 }
 
+// Smallest tile count of a launch that splits: below it the extra
+// launches (and, outside a graph, the fork and join) cost more than the
+// tails they fill.  2^20 keys in plain launches: 0.151 split against 0.131
+// ms; 2^22: 0.223 against 0.197; 2^24: 0.583 against 0.674.  In a graph
+// 2^17..2^21 keys are 3-5% slower split, 2^22 the same, 2^23 13% faster.
+constexpr uint32_t kSplitMinTilesGraph = 256, kSplitMinTilesPlain = 1024;
+
 // End of the run of launches from launch i that a graph-captured sort
 // splits into S concurrent tile ranges (see enqueue_plan); i when the launch
 // at i starts no such run (runs are at least two launches long).  pairs_io:
@@ -422,7 +436,7 @@ size_t split_run_end(const Plan& pl, size_t i, int S, int split_log2, bool pairs
     return e - i >= 2 ? e : i;
 }
 
-bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* base, uint32_t lo, uint32_t hi,
+bitonic_status enqueue_plan(DeviceState& ds, const PlanEntry& pe, void* base, uint32_t lo, uint32_t hi,
                             const KeyMaps& km, int key_bytes, int* status, cudaStream_t s, cudaEvent_t* events,
                             int* kinds, const PairIo* pio = nullptr)
 {
@@ -461,8 +475,7 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
         return ntiles;
     };
     const uint32_t wave = (uint32_t)(pe.opt.l2_prefetch * ds.tile_blocks[pl.cfg] * ds.num_sms);
-    // Concurrent tile ranges (Options::split_log2), only while the launches
-    // are captured into one of the library's graphs, where the forked
+    // Concurrent tile ranges (Options::split_log2); in a graph the forked
     // streams become parallel branches: a launch whose strides all lie below bit k - split_log2
     // works within blocks of 2^(k - split_log2) positions, and since a
     // tile's index fills the position bits outside the tile from the lowest
@@ -473,23 +486,48 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
     // 0.626 ms (each launch's last wave overlaps the other part's next
     // launch).  Four parts were slower (2^28: 13.02 ms), and so was a second
     // part started one launch behind the first (12.12 ms).
-    // Only the library's own captures split (s is then ds.capture): they
-    // begin and end inside one call under the library's lock, whereas a
-    // stream forked into a caller's capture would stay part of it until the
-    // caller ends it, and could not join another capture meanwhile.
+    // The library's own captures split into S parts on its shared fork
+    // streams (s is then ds.capture): those captures begin and end inside
+    // one call under the library's lock.  Plain launches split in two on a
+    // second stream of the caller's stream's own.  Launches that go straight
+    // into a caller's capture stay whole: a stream forked into a caller's
+    // capture would stay part of it until the caller ends it.
     int S = 1;
-    if (pe.opt.split_log2 > 0 && pe.opt.variant == 0 && !steps && !piped && !events && s == ds.capture) {
+    cudaStream_t fork_streams[kMaxSplit - 1] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kMaxSplit - 1] = {};
+    const uint32_t tiles = nl ? pl.launches[0].grid : 0;
+    if (pe.opt.split_log2 > 0 && pe.opt.variant == 0 && !steps && !piped && !events &&
+        tiles >= kSplitMinTilesGraph) {
         cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
         BT_CK(cudaStreamIsCapturing(s, &cst));
-        if (cst == cudaStreamCaptureStatusActive) S = 1 << pe.opt.split_log2;
+        if (s == ds.capture && cst == cudaStreamCaptureStatusActive) {
+            S = 1 << pe.opt.split_log2;
+            for (int q = 0; q + 1 < S; ++q) {
+                fork_streams[q] = ds.split[q];
+                join_ev[q] = ds.split_ev[q + 1];
+            }
+            fork_ev = ds.split_ev[0];
+        } else if (cst == cudaStreamCaptureStatusNone && tiles >= kSplitMinTilesPlain) {
+            DeviceState::DirectSplit& d = ds.direct_split[s];
+            if (!d.stream) {
+                BT_CK(cudaStreamCreateWithFlags(&d.stream, cudaStreamNonBlocking));
+                BT_CK(cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming));
+                BT_CK(cudaEventCreateWithFlags(&d.join, cudaEventDisableTiming));
+            }
+            S = 2;
+            fork_streams[0] = d.stream;
+            fork_ev = d.fork;
+            join_ev[0] = d.join;
+        }
     }
+    const int split_log2 = S == 4 ? 2 : (S == 2 ? 1 : 0);
     for (size_t i = 0; i < nl;) {
-        const size_t run_end = split_run_end(pl, i, S, pe.opt.split_log2, pio != nullptr);
+        const size_t run_end = split_run_end(pl, i, S, split_log2, pio != nullptr);
         if (run_end > i) {
-            BT_CK(cudaEventRecord(ds.split_ev[0], s));
-            for (int q = 1; q < S; ++q) BT_CK(cudaStreamWaitEvent(ds.split[q - 1], ds.split_ev[0], 0));
+            BT_CK(cudaEventRecord(fork_ev, s));
+            for (int q = 1; q < S; ++q) BT_CK(cudaStreamWaitEvent(fork_streams[q - 1], fork_ev, 0));
             for (int q = 0; q < S; ++q) {
-                cudaStream_t sq = q == 0 ? s : ds.split[q - 1];
+                cudaStream_t sq = q == 0 ? s : fork_streams[q - 1];
                 for (size_t a = i; a < run_end; ++a) {
                     const Launch& L = pl.launches[a];
                     const TileParams* hP = L.small ? &pl.small[L.desc] : nullptr;
@@ -504,8 +542,8 @@ bitonic_status enqueue_plan(const DeviceState& ds, const PlanEntry& pe, void* ba
                 }
             }
             for (int q = 1; q < S; ++q) {
-                BT_CK(cudaEventRecord(ds.split_ev[q], ds.split[q - 1]));
-                BT_CK(cudaStreamWaitEvent(s, ds.split_ev[q], 0));
+                BT_CK(cudaEventRecord(join_ev[q - 1], fork_streams[q - 1]));
+                BT_CK(cudaStreamWaitEvent(s, join_ev[q - 1], 0));
             }
             i = run_end;
             continue;
@@ -1300,6 +1338,12 @@ bitonic_status bitonic_release_workspace(void)
         if (kv.second.buf2) cudaFree(kv.second.buf2);
     }
     ds.ws.clear();
+    for (auto& kv : ds.direct_split) {
+        if (kv.second.stream) cudaStreamDestroy(kv.second.stream);
+        if (kv.second.fork) cudaEventDestroy(kv.second.fork);
+        if (kv.second.join) cudaEventDestroy(kv.second.join);
+    }
+    ds.direct_split.clear();
     return BITONIC_OK;
 }
 
@@ -1468,7 +1512,8 @@ bitonic_status bitonic_graph_kernels(size_t n, int pairs, int* kernels)
     if (!p.ok) return BITONIC_ERR_UNSUPPORTED;
     const bool steps = p.launches[0].kind == KIND_STEP;
     const bool fused = pairs && pairs_fused(p, o);
-    const int S = (o.split_log2 > 0 && o.variant == 0 && !steps && !o.pipeline) ? 1 << o.split_log2 : 1;
+    const int S = (o.split_log2 > 0 && o.variant == 0 && !steps && !o.pipeline &&
+                   p.launches[0].grid >= kSplitMinTilesGraph) ? 1 << o.split_log2 : 1;
     int count = 0;
     for (size_t i = 0; i < p.launches.size();) {
         const size_t e = split_run_end(p, i, S, o.split_log2, fused);

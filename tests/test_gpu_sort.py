@@ -658,15 +658,17 @@ def test_maximum_size_properties():
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("split", [1, 2])
-def test_split_tile_ranges_agree_with_oracle(split):
+@pytest.mark.parametrize("split,graphs", [(1, 1), (2, 1), (1, 0), (2, 0)])
+def test_split_tile_ranges_agree_with_oracle(split, graphs):
     # The leading launches of a graph-captured sort as 2 or 4 concurrent
     # tile ranges: sizes with several global passes, a ragged tail with
     # tiles past the last key, an off-boundary front, both directions; pairs
     # (whose first and last launches stay whole) and 8-byte keys; and a sort
     # captured inside a caller's graph (which stays unsplit), followed by a
     # split sort on another stream while that graph still exists.
-    bt.set_options(split_log2=split)
+    # graphs = 0: plain launches, split in two on a second stream of the
+    # caller's stream's own
+    bt.set_options(split_log2=split, use_graph=graphs)
     for n in [1 << 16, (1 << 20) + 3, 1 << 22, 10_000_019]:
         keys = workloads.uniform_u32(n, seed=n + 5)
         check_keys(keys, True)

@@ -185,7 +185,8 @@ def test_graph_kernels_count_the_split_ranges():
             for k in (16, 20, 24, 28):
                 plan = bt.debug_plan(1 << k)
                 his = [la[2] for la in plan["launches"]]
-                his_ok = [h < k - split and (1 << (k - 14)) % (1 << split) == 0 for h in his]
+                his_ok = [h < k - split and (1 << (k - 14)) % (1 << split) == 0 and (1 << (k - 14)) >= 256
+                          for h in his]
                 want, i = 0, 0
                 while i < len(his):
                     j = i
